@@ -1,0 +1,415 @@
+"""Benchmark of the Symanzik MD hot path on GB300.
+
+One step = one pass of the whole hot path over one 32^3x64 lattice of FP32
+compact links (w_a ~ N(0, 0.3^2), u0 = 0.87, beta = 6):
+    gauge force -> momentum step (dt) -> link step (dt) -> gauge action
+(the coefficients are computed once on the host, the staple table lives in
+the kernel parameter bank).  value = 4V links / step time in Glink/s.
+Inputs (403 MB of links, 268 MB of momenta, 268 MB of force) are larger
+than the 129 MB L2, so no flush is needed between steps.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+N > 1 runs as independent replicas, one lattice per rank (the path has no
+exchange step on one lattice per GPU); value = links of all ranks / max time.
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "32^3x64"
+METRIC = "Symanzik force Glink/s at 32^3x64 FP32 vs FP64; % HBM roofline; dH error"
+DT = 0.05
+# Algorithmic work per link-force of the literal algorithm (48 staples = 180
+# SU(3) products of 198 flops, 47 matrix additions of 18 flops, U t and the
+# projection): 36.9 kflop; compulsory bytes: FP32 12-real link read (48 B) +
+# 8-real force write (32 B).
+FLOP_PER_LINK_FORCE = 36.9e3
+BYTES_PER_LINK_FORCE = {"f32": 80, "f64": 160}
+# streaming kernels, compulsory bytes per link
+BYTES_MOM_UPDATE = {"f32": 96, "f64": 192}     # read p, read f, write p
+BYTES_LINK_UPDATE = {"f32": 128, "f64": 256}   # read U, read p, write U
+# FP32 pipe peak from unit counts and the maximum SM clock: 152 SMs x 128
+# FP32 lanes x 2 flop (FMA) x 2.070 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+CPU_SAMPLE_DIMS = (12, 12, 12, 12)
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _source_digest() -> str:
+    h = hashlib.sha256()
+    for f in ("force.cu", "su3.cuh"):
+        with open(os.path.join(ROOT, "paper_1808_02281_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _recorded_traffic():
+    """DRAM bytes per force launch from the committed ncu summary, if it was
+    taken on the current force kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "force_factored_f32_32x32x32x64.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s+source_sha256:\s*([0-9a-f]+)", text)
+    if not m or m.group(2) != _source_digest():
+        return None
+    return float(m.group(1))
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) taken while the timed region runs."""
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) != 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[2:]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def oracle_step_rate(dims=CPU_SAMPLE_DIMS, steps: int = 1):
+    """The FP64 CPU oracle running the same step (force, momentum step, link
+    step, action) on a lattice drawn like the benchmark workload; returns
+    links per second over ``steps`` steps and the seconds taken."""
+    from oracle import oracle as O
+    from paper_1808_02281_gb300 import synth
+    w = synth.WORKLOADS[WORKLOAD]
+    U = O.links_from_omega(synth.omega(dims, w["sigma"], w["seed"]))
+    p = synth.momenta(dims, seed=1)
+    c = O.coefficients(w["u0"])
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        f = O.gauge_force(dims, U, w["beta"], c)
+        p = O.md_update_momenta(p, f, DT)
+        U = O.md_update_links(U, p, DT)
+        O.gauge_action(dims, U, w["beta"], c)
+    dt = time.perf_counter() - t0
+    return 4 * synth.volume(dims) * steps / dt, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        oracle_step_rate(steps=1)
+    rates, secs = [], []
+    for _ in range(args.steps):
+        r, s = oracle_step_rate(steps=1)
+        rates.append(r)
+        secs.append(s)
+    total_links = 4 * int(np.prod(CPU_SAMPLE_DIMS)) * args.steps
+    value = total_links / sum(secs) / 1e9
+    sample = (f"one oracle step (force, momentum step, link step, action) of a "
+              f"{'x'.join(map(str, CPU_SAMPLE_DIMS))} lattice drawn like the {WORKLOAD} workload "
+              f"(w_a ~ N(0, 0.3^2), u0 0.87) per timed step; per-link work is volume independent")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Glink/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(secs) / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_dims": list(CPU_SAMPLE_DIMS)},
+        "cpu_baseline": {"value": value, "unit": "Glink/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "Glink/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+    return 0
+
+
+# ----------------------------------------------------------------- GPU arm
+
+def run_ours(args):
+    import torch
+
+    from paper_1808_02281_gb300 import build as B
+    from paper_1808_02281_gb300 import lqcd, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        B.build()
+    if dist is not None:
+        dist.barrier()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    w = synth.WORKLOADS[WORKLOAD]
+    dims = w["dims"]
+    V = synth.volume(dims)
+    nlinks = 4 * V
+    omega_np = synth.omega(dims, w["sigma"], w["seed"] + rank)
+    p_np = synth.momenta(dims, seed=1000 + rank)
+    stream = torch.cuda.current_stream(dev)
+    launches = {"n": 0}
+
+    def make(prec):
+        lat = lqcd.Lattice.symanzik(dims, w["beta"], w["u0"], prec)
+        U = lqcd.links_from_omega(lat, lqcd.algebra_to_device(lat, omega_np, device=dev))
+        mom = lqcd.algebra_to_device(lat, p_np, device=dev)
+        force = lqcd.empty_algebra(lat, dev)
+        S = torch.empty((), dtype=torch.float64, device=dev)
+        ws = lqcd.make_workspace(lat, dev)
+        return lat, U, mom, force, S, ws
+
+    def step(lat, U, mom, force, S, ws, ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        lqcd.gauge_force(lat, U, force)
+        if ev is not None:
+            ev[1].record(stream)
+        lqcd.md_update_momenta(lat, mom, force, DT)
+        if ev is not None:
+            ev[2].record(stream)
+        lqcd.md_update_links(lat, U, mom, DT)
+        if ev is not None:
+            ev[3].record(stream)
+        lqcd.gauge_action(lat, U, S, ws)
+        launches["n"] += 5  # force, momenta, links, action partials + final sum
+
+    def timed(prec, K, W, with_events):
+        lat, U, mom, force, S, ws = make(prec)
+        for _ in range(W):
+            step(lat, U, mom, force, S, ws)
+        torch.cuda.synchronize(dev)
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)] \
+            if with_events else [None] * K
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        launches["n"] = 0
+        barrier()
+        torch.cuda.synchronize(dev)
+        start.record(stream)
+        for k in range(K):
+            step(lat, U, mom, force, S, ws, evs[k])
+        stop.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        ms = start.elapsed_time(stop)
+        n_launch = launches["n"]
+        per = None
+        if with_events:
+            per = {"force": statistics.mean(e[0].elapsed_time(e[1]) for e in evs),
+                   "mom": statistics.mean(e[1].elapsed_time(e[2]) for e in evs),
+                   "links": statistics.mean(e[2].elapsed_time(e[3]) for e in evs)}
+        S_val = float(S.item())
+        del U, mom, force, S, ws
+        torch.cuda.empty_cache()
+        return ms, per, n_launch, S_val
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # headline: FP32
+    with ClockSampler(local) as clk:
+        ms, per, n_launch, S32 = timed("f32", args.steps, args.warmup, True)
+    ms = max_over_ranks(ms)
+    clocks = clk.summary()
+    value = world * nlinks * args.steps / (ms / 1e3) / 1e9
+    # FP64 beside it (fewer steps: the FP64 pipe is narrow on this part)
+    k64 = max(2, min(args.steps, 5))
+    ms64, per64, _, S64 = timed("f64", k64, max(3, min(args.warmup, 3)), True)
+    ms64 = max_over_ranks(ms64)
+
+    # end to end through the public API with host buffers
+    lat, U, mom, force, S, ws = make("f32")
+    U_host = U.detach().to("cpu").pin_memory()
+    mom_host = mom.detach().to("cpu").pin_memory()
+    S_host = torch.empty((), dtype=torch.float64).pin_memory()
+    h2d = U_host.numel() * U_host.element_size() + mom_host.numel() * mom_host.element_size()
+    d2h = 8
+    K_e2e = max(3, min(args.steps, 10))
+    for _ in range(2):
+        U.copy_(U_host, non_blocking=True)
+        mom.copy_(mom_host, non_blocking=True)
+        step(lat, U, mom, force, S, ws)
+        S_host.copy_(S, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    barrier()
+    t0 = time.perf_counter()
+    e_start, e_stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_start.record(stream)
+    for _ in range(K_e2e):
+        U.copy_(U_host, non_blocking=True)
+        mom.copy_(mom_host, non_blocking=True)
+        step(lat, U, mom, force, S, ws)
+        S_host.copy_(S, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        _ = float(S_host)
+    e_stop.record(stream)
+    torch.cuda.synchronize(dev)
+    e_ms = max_over_ranks(e_start.elapsed_time(e_stop))
+    del U, mom, force, S, ws
+    e2e_value = world * nlinks * K_e2e / (e_ms / 1e3) / 1e9
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    hbm_peak, peak_kind = _peaks()
+    force_ms = per["force"]
+    achieved_tflops = FLOP_PER_LINK_FORCE * nlinks / (force_ms / 1e3) / 1e12
+    roofline = {
+        "bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+        "frac": achieved_tflops / FP32_PEAK_TFLOPS, "traffic": _recorded_traffic(),
+        "kernel": "force_factored<float>", "units_per_launch": nlinks,
+        "algorithmic_flop_per_unit": FLOP_PER_LINK_FORCE,
+        "peak_note": "FP32 pipe: 152 SMs x 128 lanes x 2 flop x 2.070 GHz (unit counts and "
+                     "maximum clock); algorithmic flops count the literal 180-product "
+                     "algorithm, the kernel executes 134 products per link",
+        "hbm_frac_of_" + peak_kind: BYTES_PER_LINK_FORCE["f32"] * nlinks / (force_ms / 1e3) / 1e9
+        / hbm_peak,
+    }
+    streaming = {
+        "md_update_momenta": {
+            "gbs": BYTES_MOM_UPDATE["f32"] * nlinks / (per["mom"] / 1e3) / 1e9,
+            "ms": per["mom"]},
+        "md_update_links": {
+            "gbs": BYTES_LINK_UPDATE["f32"] * nlinks / (per["links"] / 1e3) / 1e9,
+            "ms": per["links"]},
+        "peak_gbs": hbm_peak, "peak_kind": peak_kind,
+    }
+    for k in ("md_update_momenta", "md_update_links"):
+        streaming[k]["frac"] = streaming[k]["gbs"] / hbm_peak
+    cpu = None
+    if world == 1 or rank == 0:
+        rate, secs = oracle_step_rate(steps=3)
+        cpu = {"value": rate / 1e9, "unit": "Glink/s", "cores": 1, "kind": "oracle",
+               "sample": f"3 oracle steps (force, momentum step, link step, action) of a "
+                         f"{'x'.join(map(str, CPU_SAMPLE_DIMS))} lattice drawn like the "
+                         f"{WORKLOAD} workload, single-threaded, {secs:.1f} s"}
+    out = {
+        "metric": METRIC, "value": value, "unit": "Glink/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "dims": list(dims), "links": nlinks,
+                   "precision": "f32 links, staples and accumulation; f64 action sum",
+                   "step": "force + momentum step + link step + action",
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (403 MB links, 268 MB momenta, 268 MB force)"},
+        "force_glinks": nlinks / (force_ms / 1e3) / 1e9,
+        "force_ms": force_ms,
+        "f64": {"value": world * nlinks * k64 / (ms64 / 1e3) / 1e9, "unit": "Glink/s",
+                "ms_per_step": ms64 / k64, "force_ms": per64["force"],
+                "force_glinks": nlinks / (per64["force"] / 1e3) / 1e9, "steps": k64},
+        "action_f32": S32, "action_f64": S64,
+        "roofline": roofline,
+        "streaming": streaming,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "Glink/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": K_e2e},
+        "gpu_launches": n_launch,
+        "clocks": clocks,
+    }
+    print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,168 @@
+/*
+ * liblqcd -- GB300 (sm_103a) molecular-dynamics hot path of the one-loop
+ * Symanzik improved gauge action (D. Li, "The Calculation of Force in Lattice
+ * Quantum Chromodynamics", Sec. II).
+ *
+ * C ABI: plain pointers and sizes.  Device buffers are owned by the caller;
+ * no entry point allocates device memory, and none synchronises the device
+ * (every kernel is enqueued on the caller's stream, `stream` = a
+ * cudaStream_t, NULL for the legacy default stream).  Every entry point
+ * returns LQCD_OK (0) or a negative LQCD_ERR_* code; arguments are checked
+ * before anything is enqueued, so on an argument error no output is touched.
+ * LQCD_ERR_CUDA reports a failed launch (the CUDA error is kept for
+ * lqcd_last_cuda_error()).
+ *
+ * Lattice and conventions
+ *   Periodic lattice L0 x L1 x L2 x L3 (x, y, z, t), site
+ *   n = x + L0*(y + L1*(z + L2*t)), V = L0*L1*L2*L3 sites, 4V links.
+ *   U_{n,mu} is the SU(3) link from n to n+mu; U_{n+mu,-mu} = U_{n,mu}^dagger.
+ *   T_a = lambda_a/2 (Gell-Mann), a = 0..7 (the paper's i = 1..8),
+ *   tr(T_a T_b) = delta_ab/2 (Eq. 18_1_29_3_0).
+ *
+ * Memory layouts (structure of arrays, `W` = 16 bytes / sizeof(real), i.e.
+ * W = 4 for LQCD_F32 (float4 lanes), W = 2 for LQCD_F64 (double2 lanes)):
+ *   links  : the first two rows of every link, 12 reals
+ *              r = (Re U00, Im U00, Re U01, Im U01, Re U02, Im U02,
+ *                   Re U10, Im U10, Re U11, Im U11, Re U12, Im U12),
+ *            real r of link (n, mu) at index ((mu*(12/W) + r/W)*V + n)*W + r%W.
+ *            The third row is rebuilt as conj(row0 x row1) on every load.
+ *            4*12*V reals.
+ *   algebra: (force, momenta, omega) 8 reals per link, component a of link
+ *            (n, mu) at ((mu*(8/W) + a/W)*V + n)*W + a%W.  4*8*V reals.
+ *   full   : (lqcd_pack_links / lqcd_unpack_links only) complex 3x3 links,
+ *            [V][4][3][3] of (re, im) pairs, row-major.  4*18*V reals.
+ *   All device pointers must be 16-byte aligned (LQCD_ERR_ALIGN otherwise).
+ *
+ * Force and momenta sign contract (Eqs. 18_7_25_1, 18_7_26_1, 18_7_25_2):
+ *   f^a_{n,mu} = -dS_G/domega^a_{n,mu}, the derivative taken along the left
+ *   perturbation U -> exp(i eps T_a) U.  As a matrix, the paper's Hermitian
+ *   force is sum_a f^a T_a = (beta/6) i (U_{n,mu} t_{n,mu})_TA, with t the
+ *   coefficient-weighted sum of the 48 staples of the link.
+ *   Molecular dynamics: p^a += dt f^a; U <- exp(i dt sum_a p^a T_a) U.
+ */
+#ifndef LQCD_H
+#define LQCD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LQCD_VERSION 1
+
+/* Status codes. */
+#define LQCD_OK 0
+#define LQCD_ERR_ARG (-1)         /* NULL pointer, unknown enum, bad parameter  */
+#define LQCD_ERR_DIMS (-2)        /* extent < 1 or 4V*12 reals do not fit int64  */
+#define LQCD_ERR_ALIGN (-3)       /* a device pointer is not 16-byte aligned    */
+#define LQCD_ERR_WORKSPACE (-4)   /* workspace NULL or smaller than required    */
+#define LQCD_ERR_CUDA (-5)        /* a CUDA runtime call or launch failed       */
+#define LQCD_ERR_UNSUPPORTED (-6) /* option not available for this precision    */
+
+/* Precision of every real in every buffer passed with a descriptor. */
+#define LQCD_F32 0
+#define LQCD_F64 1
+
+/* Force algorithms (lqcd_desc.force_algo). */
+#define LQCD_FORCE_AUTO 0     /* fastest available (currently FACTORED)         */
+#define LQCD_FORCE_PATHS 1    /* one thread per link walks the 48 staples of a
+                                 per-direction path table (plain form)          */
+#define LQCD_FORCE_FACTORED 2 /* one thread per link, staples regrouped by their
+                                 shared end links (134 instead of 180 matrix
+                                 products per link)                             */
+
+/* Problem descriptor.  beta is the inverse coupling of Eq. 18_6_4_1 and
+ * (c_plaq, c_rect, c_cube) are the loop coefficients c_P of Eq. 18_3_27_30;
+ * lqcd_symanzik_coefficients() fills them from the tadpole factor u0. */
+typedef struct lqcd_desc {
+    int32_t dims[4];    /* L0..L3, each >= 1                                 */
+    int32_t precision;  /* LQCD_F32 or LQCD_F64                              */
+    int32_t force_algo; /* LQCD_FORCE_*                                      */
+    double beta;
+    double c_plaq;
+    double c_rect;
+    double c_cube;
+} lqcd_desc;
+
+/* Loop coefficients of Eq. 18_3_27_30 (host only, no device work):
+ *   alpha_s = -4 ln(u0) / 3.06839,  c_plaq = 1,
+ *   c_rect = -(1 + 0.4805 alpha_s) / (20 u0^2),
+ *   c_cube = -2 * 0.03325 alpha_s / u0^2   (the printed factor 2 is kept).
+ * u0 must be finite and > 0.  Any output pointer may be NULL. */
+int lqcd_symanzik_coefficients(double u0, double *alpha_s, double *c_plaq, double *c_rect,
+                               double *c_cube);
+
+/* Links from their algebra parameters, U_{n,mu} = exp(i sum_a omega^a T_a)
+ * (Eq. 18_1_29_3).  omega: algebra layout (device, read); links: link layout
+ * (device, written).  The exponential is the Cayley-Hamilton form
+ * f0 + f1 Q + f2 Q^2 (exact for 3x3), coefficients by their power series. */
+int lqcd_links_from_omega(const lqcd_desc *desc, const void *omega, void *links, void *stream);
+
+/* Gauge force of the Symanzik action for every link (Eq. 18_7_25_2 and the
+ * force algorithm of Sec. II): f^a = -dS/domega^a.  links: link layout
+ * (device, read); force: algebra layout (device, written).  workspace may be
+ * NULL (no algorithm needs one yet; lqcd_workspace_bytes reports 0). */
+int lqcd_gauge_force(const lqcd_desc *desc, const void *links, void *force, void *workspace,
+                     size_t workspace_bytes, void *stream);
+
+/* The force, fused with the momentum step: p^a += dt f^a, without storing f.
+ * links: link layout (read); mom: algebra layout (read and written). */
+int lqcd_gauge_force_update_momenta(const lqcd_desc *desc, const void *links, void *mom,
+                                    double dt, void *stream);
+
+/* Gauge action S_G = (beta/3) sum_n sum_{34 loops P} c_P [3 - Re tr P_n]
+ * (Eq. 18_6_4_1).  links: link layout (device, read).  action: ONE double in
+ * device memory (written, FP64 in both precisions: per-loop terms and all
+ * sums are accumulated in double, in a fixed order, so the result is
+ * bitwise reproducible).  workspace: device scratch of at least
+ * lqcd_workspace_bytes(desc) bytes, 256-byte aligned, used for per-block
+ * partial sums. */
+int lqcd_gauge_action(const lqcd_desc *desc, const void *links, double *action, void *workspace,
+                      size_t workspace_bytes, void *stream);
+
+/* Kinetic term K = (1/2) sum_{links, a} p^a p^a of the MD Hamiltonian, in
+ * double, same reduction as lqcd_gauge_action.  mom: algebra layout (read);
+ * energy: one double in device memory (written). */
+int lqcd_kinetic_energy(const lqcd_desc *desc, const void *mom, double *energy, void *workspace,
+                        size_t workspace_bytes, void *stream);
+
+/* Momentum step p^a += dt f^a for every link (the equation of motion of
+ * H = K + S_G with f = -dS/domega, Eq. 18_7_25_1).  mom: algebra layout (read
+ * and written); force: algebra layout (read).  mom == force is rejected. */
+int lqcd_md_update_momenta(const lqcd_desc *desc, void *mom, const void *force, double dt,
+                           void *stream);
+
+/* Link step U <- exp(i dt sum_a p^a T_a) U for every link (the flow of the
+ * left parametrisation of Eq. 18_1_29_3), then Gram-Schmidt of rows 0, 1
+ * (row 2 is always rebuilt as conj(row0 x row1)).  links: link layout (read
+ * and written); mom: algebra layout (read). */
+int lqcd_md_update_links(const lqcd_desc *desc, void *links, const void *mom, double dt,
+                         void *stream);
+
+/* Layout conversions between full complex 3x3 links ([V][4][3][3] (re, im))
+ * and the compact link layout, in the descriptor's precision.  pack drops
+ * row 2 (the input must be SU(3) for the result to mean the same links);
+ * unpack rebuilds it. */
+int lqcd_pack_links(const lqcd_desc *desc, const void *full, void *links, void *stream);
+int lqcd_unpack_links(const lqcd_desc *desc, const void *links, void *full, void *stream);
+
+/* Bytes of device workspace that lqcd_gauge_action / lqcd_kinetic_energy
+ * need for this descriptor on the current device (0 on a bad descriptor). */
+size_t lqcd_workspace_bytes(const lqcd_desc *desc);
+
+/* Human-readable text of a status code (static storage). */
+const char *lqcd_strerror(int status);
+
+/* The last CUDA error code seen by this library on the calling thread. */
+int lqcd_last_cuda_error(void);
+
+/* LQCD_VERSION of the built library. */
+int lqcd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LQCD_H */

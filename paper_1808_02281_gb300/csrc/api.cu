@@ -1,0 +1,273 @@
+// C-ABI entry points of liblqcd (declared in include/lqcd.h): argument
+// checks, then one enqueue on the caller's stream.  Nothing here allocates
+// device memory or synchronises.
+#include <cmath>
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace {
+
+thread_local int g_last_cuda_error = 0;
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return LQCD_OK;
+    g_last_cuda_error = (int)e;
+    return LQCD_ERR_CUDA;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+int check_desc(const lqcd_desc *d)
+{
+    if (d == nullptr) return LQCD_ERR_ARG;
+    if (d->precision != LQCD_F32 && d->precision != LQCD_F64) return LQCD_ERR_ARG;
+    if (d->force_algo < LQCD_FORCE_AUTO || d->force_algo > LQCD_FORCE_FACTORED) return LQCD_ERR_ARG;
+    if (!std::isfinite(d->beta) || !std::isfinite(d->c_plaq) || !std::isfinite(d->c_rect) ||
+        !std::isfinite(d->c_cube))
+        return LQCD_ERR_ARG;
+    // every extent >= 1 and 4 * 18 * V reals addressable with int64 offsets
+    const int64_t limit = ((int64_t)1 << 62) / 72;
+    int64_t V = 1;
+    for (int i = 0; i < 4; ++i) {
+        if (d->dims[i] < 1) return LQCD_ERR_DIMS;
+        V *= d->dims[i];
+        if (V > limit) return LQCD_ERR_DIMS;
+    }
+    return LQCD_OK;
+}
+
+int check_ptrs(std::initializer_list<const void *> ps)
+{
+    for (const void *p : ps) {
+        if (p == nullptr) return LQCD_ERR_ARG;
+        if (!aligned16(p)) return LQCD_ERR_ALIGN;
+    }
+    return LQCD_OK;
+}
+
+void copy_dims(int out[4], const lqcd_desc *d)
+{
+    for (int i = 0; i < 4; ++i) out[i] = d->dims[i];
+}
+
+cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
+
+int reduction_setup(const lqcd_desc *desc, void *workspace, size_t workspace_bytes, int *blocks)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    const int b = lqcd::reduction_blocks(dev);
+    if (b <= 0) return cuda_status(cudaGetLastError() == cudaSuccess ? cudaErrorUnknown : cudaGetLastError());
+    if (workspace == nullptr || ((uintptr_t)workspace & 255u) != 0) return LQCD_ERR_WORKSPACE;
+    if (workspace_bytes < (size_t)b * sizeof(double)) return LQCD_ERR_WORKSPACE;
+    *blocks = b;
+    (void)desc;
+    return LQCD_OK;
+}
+
+int force_common(const lqcd_desc *desc, const void *links, void *force, void *mom, double dt,
+                 void *stream)
+{
+    lqcd::ForceArgs a{};
+    copy_dims(a.dims, desc);
+    a.precision = desc->precision;
+    a.algo = desc->force_algo == LQCD_FORCE_AUTO ? LQCD_FORCE_FACTORED : desc->force_algo;
+    a.beta = desc->beta;
+    a.c_plaq = desc->c_plaq;
+    a.c_rect = desc->c_rect;
+    a.c_cube = desc->c_cube;
+    a.links = links;
+    a.force = force;
+    a.mom = mom;
+    a.dt = dt;
+    return cuda_status(lqcd::launch_force(a, as_stream(stream)));
+}
+
+} // namespace
+
+extern "C" {
+
+int lqcd_symanzik_coefficients(double u0, double *alpha_s, double *c_plaq, double *c_rect,
+                               double *c_cube)
+{
+    if (!std::isfinite(u0) || !(u0 > 0.0)) return LQCD_ERR_ARG;
+    const double as = -4.0 * std::log(u0) / 3.06839;
+    if (alpha_s) *alpha_s = as;
+    if (c_plaq) *c_plaq = 1.0;
+    if (c_rect) *c_rect = -(1.0 + 0.4805 * as) / (20.0 * u0 * u0);
+    if (c_cube) *c_cube = -2.0 * 0.03325 * as / (u0 * u0);
+    return LQCD_OK;
+}
+
+int lqcd_links_from_omega(const lqcd_desc *desc, const void *omega, void *links, void *stream)
+{
+    int s = check_desc(desc);
+    if (s) return s;
+    if ((s = check_ptrs({omega, links}))) return s;
+    if (omega == links) return LQCD_ERR_ARG;
+    lqcd::MdArgs a{};
+    copy_dims(a.dims, desc);
+    a.precision = desc->precision;
+    a.links = links;
+    a.mom = omega;
+    return cuda_status(lqcd::launch_links_from_omega(a, as_stream(stream)));
+}
+
+int lqcd_gauge_force(const lqcd_desc *desc, const void *links, void *force, void *workspace,
+                     size_t workspace_bytes, void *stream)
+{
+    (void)workspace;
+    (void)workspace_bytes;
+    int s = check_desc(desc);
+    if (s) return s;
+    if ((s = check_ptrs({links, force}))) return s;
+    if (links == force) return LQCD_ERR_ARG;
+    return force_common(desc, links, force, nullptr, 0.0, stream);
+}
+
+int lqcd_gauge_force_update_momenta(const lqcd_desc *desc, const void *links, void *mom,
+                                    double dt, void *stream)
+{
+    int s = check_desc(desc);
+    if (s) return s;
+    if ((s = check_ptrs({links, mom}))) return s;
+    if (links == mom || !std::isfinite(dt)) return LQCD_ERR_ARG;
+    return force_common(desc, links, nullptr, mom, dt, stream);
+}
+
+int lqcd_gauge_action(const lqcd_desc *desc, const void *links, double *action, void *workspace,
+                      size_t workspace_bytes, void *stream)
+{
+    int s = check_desc(desc);
+    if (s) return s;
+    if ((s = check_ptrs({links}))) return s;
+    if (action == nullptr) return LQCD_ERR_ARG;
+    if (((uintptr_t)action & 7u) != 0) return LQCD_ERR_ALIGN;
+    int blocks = 0;
+    if ((s = reduction_setup(desc, workspace, workspace_bytes, &blocks))) return s;
+    lqcd::ReduceArgs a{};
+    copy_dims(a.dims, desc);
+    a.precision = desc->precision;
+    a.links = links;
+    a.c[0] = desc->c_plaq;
+    a.c[1] = desc->c_rect;
+    a.c[2] = desc->c_cube;
+    a.scale = desc->beta / 3.0;
+    a.partials = static_cast<double *>(workspace);
+    a.blocks = blocks;
+    a.out = action;
+    return cuda_status(lqcd::launch_action(a, as_stream(stream)));
+}
+
+int lqcd_kinetic_energy(const lqcd_desc *desc, const void *mom, double *energy, void *workspace,
+                        size_t workspace_bytes, void *stream)
+{
+    int s = check_desc(desc);
+    if (s) return s;
+    if ((s = check_ptrs({mom}))) return s;
+    if (energy == nullptr) return LQCD_ERR_ARG;
+    if (((uintptr_t)energy & 7u) != 0) return LQCD_ERR_ALIGN;
+    int blocks = 0;
+    if ((s = reduction_setup(desc, workspace, workspace_bytes, &blocks))) return s;
+    lqcd::ReduceArgs a{};
+    copy_dims(a.dims, desc);
+    a.precision = desc->precision;
+    a.mom = mom;
+    a.partials = static_cast<double *>(workspace);
+    a.blocks = blocks;
+    a.out = energy;
+    return cuda_status(lqcd::launch_kinetic(a, as_stream(stream)));
+}
+
+int lqcd_md_update_momenta(const lqcd_desc *desc, void *mom, const void *force, double dt,
+                           void *stream)
+{
+    int s = check_desc(desc);
+    if (s) return s;
+    if ((s = check_ptrs({mom, force}))) return s;
+    if (mom == force || !std::isfinite(dt)) return LQCD_ERR_ARG;
+    lqcd::MdArgs a{};
+    copy_dims(a.dims, desc);
+    a.precision = desc->precision;
+    a.mom_out = mom;
+    a.force = force;
+    a.dt = dt;
+    return cuda_status(lqcd::launch_update_momenta(a, as_stream(stream)));
+}
+
+int lqcd_md_update_links(const lqcd_desc *desc, void *links, const void *mom, double dt,
+                         void *stream)
+{
+    int s = check_desc(desc);
+    if (s) return s;
+    if ((s = check_ptrs({links, mom}))) return s;
+    if (links == mom || !std::isfinite(dt)) return LQCD_ERR_ARG;
+    lqcd::MdArgs a{};
+    copy_dims(a.dims, desc);
+    a.precision = desc->precision;
+    a.links = links;
+    a.mom = mom;
+    a.dt = dt;
+    return cuda_status(lqcd::launch_update_links(a, as_stream(stream)));
+}
+
+int lqcd_pack_links(const lqcd_desc *desc, const void *full, void *links, void *stream)
+{
+    int s = check_desc(desc);
+    if (s) return s;
+    if ((s = check_ptrs({full, links}))) return s;
+    if (full == links) return LQCD_ERR_ARG;
+    lqcd::MdArgs a{};
+    copy_dims(a.dims, desc);
+    a.precision = desc->precision;
+    a.full_in = full;
+    a.links = links;
+    return cuda_status(lqcd::launch_pack(a, as_stream(stream)));
+}
+
+int lqcd_unpack_links(const lqcd_desc *desc, const void *links, void *full, void *stream)
+{
+    int s = check_desc(desc);
+    if (s) return s;
+    if ((s = check_ptrs({full, links}))) return s;
+    if (full == links) return LQCD_ERR_ARG;
+    lqcd::MdArgs a{};
+    copy_dims(a.dims, desc);
+    a.precision = desc->precision;
+    a.links = const_cast<void *>(links);
+    a.full_out = full;
+    return cuda_status(lqcd::launch_unpack(a, as_stream(stream)));
+}
+
+size_t lqcd_workspace_bytes(const lqcd_desc *desc)
+{
+    if (check_desc(desc) != LQCD_OK) return 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    const int b = lqcd::reduction_blocks(dev);
+    if (b <= 0) return 0;
+    return ((size_t)b * sizeof(double) + 255) & ~(size_t)255;
+}
+
+const char *lqcd_strerror(int status)
+{
+    switch (status) {
+    case LQCD_OK: return "success";
+    case LQCD_ERR_ARG: return "invalid argument";
+    case LQCD_ERR_DIMS: return "invalid lattice extents";
+    case LQCD_ERR_ALIGN: return "device pointer not 16-byte aligned";
+    case LQCD_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case LQCD_ERR_CUDA: return "CUDA runtime error";
+    case LQCD_ERR_UNSUPPORTED: return "unsupported option";
+    default: return "unknown status";
+    }
+}
+
+int lqcd_last_cuda_error(void) { return g_last_cuda_error; }
+
+int lqcd_version(void) { return LQCD_VERSION; }
+
+} // extern "C"

@@ -1,0 +1,89 @@
+// Internal launch interface between the C-ABI layer (api.cu) and the kernel
+// translation units.  Host-side C++ only; no torch types.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/lqcd.h"
+
+namespace lqcd {
+
+// One staple of the path kernel: cls (0 plaquette, 1 rectangle, 2 cube),
+// len (3 or 5) signed directions +-(mu+1), walked from k + rho.
+struct Staple {
+    int8_t cls;
+    int8_t len;
+    int8_t d[6];
+};
+
+struct StapleTable {
+    Staple s[4][48];
+    int count;
+};
+
+const StapleTable &staple_table();
+
+struct ForceArgs {
+    int dims[4];
+    int precision;
+    int algo;
+    double beta, c_plaq, c_rect, c_cube;
+    const void *links;
+    void *force; // written when mom == nullptr
+    void *mom;   // when set: mom += dt * f, force not written
+    double dt;
+};
+
+cudaError_t launch_force(const ForceArgs &a, cudaStream_t st);
+
+// The 34 loops of the action kernel: cls, len (4 or 6), signed directions.
+struct Loop {
+    int8_t cls;
+    int8_t len;
+    int8_t d[6];
+};
+
+struct LoopTable {
+    Loop l[34];
+    int count;
+};
+
+const LoopTable &loop_table();
+
+struct ReduceArgs {
+    int dims[4];
+    int precision;
+    const void *links; // action
+    const void *mom;   // kinetic energy
+    double c[3];
+    double scale;      // result = scale * sum
+    double *partials;  // workspace, one double per block
+    int blocks;
+    double *out;
+};
+
+int reduction_blocks(int device);
+cudaError_t launch_action(const ReduceArgs &a, cudaStream_t st);
+cudaError_t launch_kinetic(const ReduceArgs &a, cudaStream_t st);
+
+struct MdArgs {
+    int dims[4];
+    int precision;
+    void *links;
+    const void *mom;
+    const void *force;
+    void *mom_out;
+    const void *full_in;
+    void *full_out;
+    double dt;
+};
+
+cudaError_t launch_update_momenta(const MdArgs &a, cudaStream_t st);
+cudaError_t launch_update_links(const MdArgs &a, cudaStream_t st);
+cudaError_t launch_links_from_omega(const MdArgs &a, cudaStream_t st);
+cudaError_t launch_pack(const MdArgs &a, cudaStream_t st);
+cudaError_t launch_unpack(const MdArgs &a, cudaStream_t st);
+
+} // namespace lqcd

@@ -1,0 +1,205 @@
+// Molecular-dynamics steps and layout conversions, all streaming kernels
+// (one thread per link or per 16-byte lane, grid-stride, coalesced 16-byte
+// loads and stores of the structure-of-arrays planes).
+//   momentum step  p^a += dt f^a                      (f = -dS/domega, Eq. 18_7_25_1)
+//   link step      U <- exp(i dt sum_a p^a T_a) U     (left flow of Eq. 18_1_29_3)
+//   links from omega  U = exp(i sum_a omega^a T_a)    (Eq. 18_1_29_3)
+//   pack / unpack  full 3x3 complex <-> first two rows
+#include "kernels.h"
+#include "su3.cuh"
+
+namespace lqcd {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+int64_t volume(const int dims[4])
+{
+    return (int64_t)dims[0] * dims[1] * dims[2] * dims[3];
+}
+
+unsigned grid_for(int64_t items)
+{
+    int64_t g = (items + kBlock - 1) / kBlock;
+    if (g < 1) g = 1;
+    if (g > ((int64_t)1 << 30)) g = (int64_t)1 << 30;
+    return (unsigned)g;
+}
+
+// p += dt f over 16-byte lanes of the algebra planes.
+template <typename R>
+__global__ void __launch_bounds__(kBlock) update_momenta(typename Vec<R>::type *__restrict__ p,
+                                                         const typename Vec<R>::type *__restrict__ f,
+                                                         int64_t lanes, R dt)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < lanes;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        auto a = p[i];
+        const auto b = __ldg(f + i);
+        if constexpr (Vec<R>::W == 4) {
+            a.x = fma(dt, b.x, a.x);
+            a.y = fma(dt, b.y, a.y);
+            a.z = fma(dt, b.z, a.z);
+            a.w = fma(dt, b.w, a.w);
+        } else {
+            a.x = fma(dt, b.x, a.x);
+            a.y = fma(dt, b.y, a.y);
+        }
+        p[i] = a;
+    }
+}
+
+// U <- exp(i dt P) U (FROM_UNIT: U = exp(i dt P)), rows 0 and 1 only, then
+// Gram-Schmidt.  The link and algebra planes share the site index.
+template <typename R, bool FROM_UNIT>
+__global__ void __launch_bounds__(kBlock) update_links(R *__restrict__ links,
+                                                       const R *__restrict__ mom, int64_t V, R dt)
+{
+    const int64_t nlinks = 4 * V;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nlinks;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int mu = (int)(i / V);
+        const int64_t n = i - mu * V;
+        R p[8];
+        load_algebra(mom, V, mu, n, p);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) p[c] *= dt;
+        const Mat<R> e = exp_i_hermitian(algebra_matrix(p));
+        Mat<R> u;
+        if constexpr (FROM_UNIT) {
+            u = e;
+        } else {
+            const Mat<R> v = load_link(links, V, mu, n);
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    R re = R(0), im = R(0);
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        re = fma(e.re[r][k], v.re[k][j], re);
+                        re = fma(-e.im[r][k], v.im[k][j], re);
+                        im = fma(e.re[r][k], v.im[k][j], im);
+                        im = fma(e.im[r][k], v.re[k][j], im);
+                    }
+                    u.re[r][j] = re;
+                    u.im[r][j] = im;
+                }
+        }
+        reunitarise(u);
+        store_link(links, V, mu, n, u);
+    }
+}
+
+// full [V][4][3][3] (re, im) -> compact link layout (rows 0, 1)
+template <typename R>
+__global__ void __launch_bounds__(kBlock) pack(const R *__restrict__ full, R *__restrict__ links,
+                                               int64_t V)
+{
+    const int64_t nlinks = 4 * V;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nlinks;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int mu = (int)(i / V);
+        const int64_t n = i - mu * V;
+        const R *src = full + (n * 4 + mu) * 18;
+        Mat<R> u;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                u.re[r][j] = src[(3 * r + j) * 2];
+                u.im[r][j] = src[(3 * r + j) * 2 + 1];
+            }
+        store_link(links, V, mu, n, u);
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) unpack(const R *__restrict__ links, R *__restrict__ full,
+                                                 int64_t V)
+{
+    const int64_t nlinks = 4 * V;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nlinks;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int mu = (int)(i / V);
+        const int64_t n = i - mu * V;
+        const Mat<R> u = load_link(links, V, mu, n);
+        R *dst = full + (n * 4 + mu) * 18;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                dst[(3 * r + j) * 2] = u.re[r][j];
+                dst[(3 * r + j) * 2 + 1] = u.im[r][j];
+            }
+    }
+}
+
+} // namespace
+
+cudaError_t launch_update_momenta(const MdArgs &a, cudaStream_t st)
+{
+    const int64_t V = volume(a.dims);
+    if (a.precision == LQCD_F64) {
+        const int64_t lanes = 4 * 8 * V / 2;
+        update_momenta<double><<<grid_for(lanes), kBlock, 0, st>>>(
+            static_cast<double2 *>(a.mom_out), static_cast<const double2 *>(a.force), lanes, a.dt);
+    } else {
+        const int64_t lanes = 4 * 8 * V / 4;
+        update_momenta<float><<<grid_for(lanes), kBlock, 0, st>>>(
+            static_cast<float4 *>(a.mom_out), static_cast<const float4 *>(a.force), lanes,
+            (float)a.dt);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_links(const MdArgs &a, cudaStream_t st)
+{
+    const int64_t V = volume(a.dims);
+    if (a.precision == LQCD_F64)
+        update_links<double, false><<<grid_for(4 * V), kBlock, 0, st>>>(
+            static_cast<double *>(a.links), static_cast<const double *>(a.mom), V, a.dt);
+    else
+        update_links<float, false><<<grid_for(4 * V), kBlock, 0, st>>>(
+            static_cast<float *>(a.links), static_cast<const float *>(a.mom), V, (float)a.dt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_links_from_omega(const MdArgs &a, cudaStream_t st)
+{
+    const int64_t V = volume(a.dims);
+    if (a.precision == LQCD_F64)
+        update_links<double, true><<<grid_for(4 * V), kBlock, 0, st>>>(
+            static_cast<double *>(a.links), static_cast<const double *>(a.mom), V, 1.0);
+    else
+        update_links<float, true><<<grid_for(4 * V), kBlock, 0, st>>>(
+            static_cast<float *>(a.links), static_cast<const float *>(a.mom), V, 1.0f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const MdArgs &a, cudaStream_t st)
+{
+    const int64_t V = volume(a.dims);
+    if (a.precision == LQCD_F64)
+        pack<double><<<grid_for(4 * V), kBlock, 0, st>>>(static_cast<const double *>(a.full_in),
+                                                          static_cast<double *>(a.links), V);
+    else
+        pack<float><<<grid_for(4 * V), kBlock, 0, st>>>(static_cast<const float *>(a.full_in),
+                                                         static_cast<float *>(a.links), V);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const MdArgs &a, cudaStream_t st)
+{
+    const int64_t V = volume(a.dims);
+    if (a.precision == LQCD_F64)
+        unpack<double><<<grid_for(4 * V), kBlock, 0, st>>>(static_cast<const double *>(a.links),
+                                                            static_cast<double *>(a.full_out), V);
+    else
+        unpack<float><<<grid_for(4 * V), kBlock, 0, st>>>(static_cast<const float *>(a.links),
+                                                           static_cast<float *>(a.full_out), V);
+    return cudaGetLastError();
+}
+
+} // namespace lqcd

@@ -1,0 +1,321 @@
+"""Thin Python binding of liblqcd (include/lqcd.h): argument marshalling only.
+
+Every computation runs in the CUDA kernels of ``liblqcd.so``; torch supplies
+device memory and the current CUDA stream.  There is no CPU fallback: if the
+library is missing or a call fails, an exception is raised.
+
+Tensor layouts (W = 4 for float32, 2 for float64; see include/lqcd.h):
+  links    [4, 12 // W, V, W]   first two rows of every SU(3) link
+  algebra  [4,  8 // W, V, W]   force, momenta, omega (components along T_a)
+  full     [V, 4, 3, 3, 2]      complex 3x3 links as (re, im)
+Helpers convert site-major numpy arrays [V, 4, 8] / complex [V, 4, 3, 3]
+to and from these layouts (pure reshapes).
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblqcd.so")
+
+F32, F64 = 0, 1
+FORCE_AUTO, FORCE_PATHS, FORCE_FACTORED = 0, 1, 2
+
+
+class LqcdError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        msg = _lib().lqcd_strerror(status).decode()
+        if status == -5:
+            msg += f" (cudaError {_lib().lqcd_last_cuda_error()})"
+        super().__init__(f"{what}: {msg} [{status}]")
+        self.status = status
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int32 * 4), ("precision", ctypes.c_int32),
+                ("force_algo", ctypes.c_int32), ("beta", ctypes.c_double),
+                ("c_plaq", ctypes.c_double), ("c_rect", ctypes.c_double),
+                ("c_cube", ctypes.c_double)]
+
+
+_LIB = None
+_EXPORTS = {
+    "lqcd_symanzik_coefficients": (ctypes.c_int, [ctypes.c_double] + [ctypes.POINTER(ctypes.c_double)] * 4),
+    "lqcd_links_from_omega": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "lqcd_gauge_force": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_size_t, ctypes.c_void_p]),
+    "lqcd_gauge_force_update_momenta": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p,
+                                                       ctypes.c_double, ctypes.c_void_p]),
+    "lqcd_gauge_action": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_size_t, ctypes.c_void_p]),
+    "lqcd_kinetic_energy": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_size_t, ctypes.c_void_p]),
+    "lqcd_md_update_momenta": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_double, ctypes.c_void_p]),
+    "lqcd_md_update_links": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_double, ctypes.c_void_p]),
+    "lqcd_pack_links": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "lqcd_unpack_links": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "lqcd_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(Desc)]),
+    "lqcd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "lqcd_last_cuda_error": (ctypes.c_int, []),
+    "lqcd_version": (ctypes.c_int, []),
+}
+
+
+def _lib():
+    """Load liblqcd.so; raise if it has not been built (no fallback)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_1808_02281_gb300.build`")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _EXPORTS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def library_path() -> str:
+    _lib()
+    return LIB_PATH
+
+
+def symanzik_coefficients(u0: float):
+    """(alpha_s, c_plaq, c_rect, c_cube) of Eq. 18_3_27_30 from u0."""
+    out = [ctypes.c_double() for _ in range(4)]
+    st = _lib().lqcd_symanzik_coefficients(float(u0), *[ctypes.byref(o) for o in out])
+    if st:
+        raise LqcdError(st, "lqcd_symanzik_coefficients")
+    return tuple(o.value for o in out)
+
+
+@dataclasses.dataclass
+class Lattice:
+    """A periodic lattice plus the action parameters (lqcd_desc)."""
+    dims: tuple
+    precision: str = "f32"   # "f32" or "f64"
+    beta: float = 6.0
+    c_plaq: float = 1.0
+    c_rect: float = 0.0
+    c_cube: float = 0.0
+    force_algo: int = FORCE_AUTO
+
+    @classmethod
+    def symanzik(cls, dims, beta: float = 6.0, u0: float = 0.87, precision: str = "f32",
+                 force_algo: int = FORCE_AUTO) -> "Lattice":
+        _, cp, cr, cc = symanzik_coefficients(u0)
+        return cls(tuple(int(d) for d in dims), precision, float(beta), cp, cr, cc, force_algo)
+
+    @property
+    def V(self) -> int:
+        return int(np.prod(self.dims))
+
+    @property
+    def dtype(self):
+        return torch.float32 if self.precision == "f32" else torch.float64
+
+    @property
+    def W(self) -> int:
+        return 4 if self.precision == "f32" else 2
+
+    @property
+    def link_shape(self):
+        return (4, 12 // self.W, self.V, self.W)
+
+    @property
+    def algebra_shape(self):
+        return (4, 8 // self.W, self.V, self.W)
+
+    def desc(self) -> Desc:
+        d = Desc()
+        for i in range(4):
+            d.dims[i] = int(self.dims[i])
+        d.precision = F32 if self.precision == "f32" else F64
+        d.force_algo = int(self.force_algo)
+        d.beta = self.beta
+        d.c_plaq, d.c_rect, d.c_cube = self.c_plaq, self.c_rect, self.c_cube
+        return d
+
+    def with_(self, **kw) -> "Lattice":
+        return dataclasses.replace(self, **kw)
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(t: torch.Tensor, lat: Lattice, shape, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != lat.dtype:
+        raise TypeError(f"{name} must be {lat.dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous with shape {tuple(shape)}, got {tuple(t.shape)}")
+
+
+def _call(name: str, *args):
+    st = getattr(_lib(), name)(*args)
+    if st:
+        raise LqcdError(st, name)
+
+
+def _ptr(t: torch.Tensor) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def empty_links(lat: Lattice, device=None) -> torch.Tensor:
+    return torch.empty(lat.link_shape, dtype=lat.dtype, device=device or "cuda")
+
+
+def empty_algebra(lat: Lattice, device=None) -> torch.Tensor:
+    return torch.empty(lat.algebra_shape, dtype=lat.dtype, device=device or "cuda")
+
+
+def workspace_bytes(lat: Lattice) -> int:
+    d = lat.desc()
+    return int(_lib().lqcd_workspace_bytes(ctypes.byref(d)))
+
+
+def make_workspace(lat: Lattice, device=None) -> torch.Tensor:
+    n = max(workspace_bytes(lat), 256)
+    return torch.empty(n, dtype=torch.uint8, device=device or "cuda")
+
+
+def links_from_omega(lat: Lattice, omega: torch.Tensor, out: torch.Tensor | None = None,
+                     stream=None) -> torch.Tensor:
+    """U = exp(i omega.T) for every link (Eq. 18_1_29_3)."""
+    _check(omega, lat, lat.algebra_shape, "omega")
+    out = empty_links(lat, omega.device) if out is None else out
+    _check(out, lat, lat.link_shape, "links")
+    d = lat.desc()
+    _call("lqcd_links_from_omega", ctypes.byref(d), _ptr(omega), _ptr(out), _stream(stream))
+    return out
+
+
+def gauge_force(lat: Lattice, links: torch.Tensor, out: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+    """f^a = -dS/domega^a for every link (algebra layout)."""
+    _check(links, lat, lat.link_shape, "links")
+    out = empty_algebra(lat, links.device) if out is None else out
+    _check(out, lat, lat.algebra_shape, "force")
+    d = lat.desc()
+    _call("lqcd_gauge_force", ctypes.byref(d), _ptr(links), _ptr(out), None, 0, _stream(stream))
+    return out
+
+
+def gauge_force_update_momenta(lat: Lattice, links: torch.Tensor, mom: torch.Tensor, dt: float,
+                               stream=None) -> torch.Tensor:
+    """mom += dt * f, the force never stored."""
+    _check(links, lat, lat.link_shape, "links")
+    _check(mom, lat, lat.algebra_shape, "mom")
+    d = lat.desc()
+    _call("lqcd_gauge_force_update_momenta", ctypes.byref(d), _ptr(links), _ptr(mom),
+          float(dt), _stream(stream))
+    return mom
+
+
+def gauge_action(lat: Lattice, links: torch.Tensor, out: torch.Tensor | None = None,
+                 workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """S_G (FP64, 0-d device tensor), Eq. 18_6_4_1."""
+    _check(links, lat, lat.link_shape, "links")
+    out = torch.empty((), dtype=torch.float64, device=links.device) if out is None else out
+    ws = make_workspace(lat, links.device) if workspace is None else workspace
+    d = lat.desc()
+    _call("lqcd_gauge_action", ctypes.byref(d), _ptr(links), _ptr(out), _ptr(ws), ws.numel(),
+          _stream(stream))
+    return out
+
+
+def kinetic_energy(lat: Lattice, mom: torch.Tensor, out: torch.Tensor | None = None,
+                   workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """K = sum p^2 / 2 (FP64, 0-d device tensor)."""
+    _check(mom, lat, lat.algebra_shape, "mom")
+    out = torch.empty((), dtype=torch.float64, device=mom.device) if out is None else out
+    ws = make_workspace(lat, mom.device) if workspace is None else workspace
+    d = lat.desc()
+    _call("lqcd_kinetic_energy", ctypes.byref(d), _ptr(mom), _ptr(out), _ptr(ws), ws.numel(),
+          _stream(stream))
+    return out
+
+
+def md_update_momenta(lat: Lattice, mom: torch.Tensor, force: torch.Tensor, dt: float,
+                      stream=None) -> torch.Tensor:
+    _check(mom, lat, lat.algebra_shape, "mom")
+    _check(force, lat, lat.algebra_shape, "force")
+    d = lat.desc()
+    _call("lqcd_md_update_momenta", ctypes.byref(d), _ptr(mom), _ptr(force), float(dt),
+          _stream(stream))
+    return mom
+
+
+def md_update_links(lat: Lattice, links: torch.Tensor, mom: torch.Tensor, dt: float,
+                    stream=None) -> torch.Tensor:
+    _check(links, lat, lat.link_shape, "links")
+    _check(mom, lat, lat.algebra_shape, "mom")
+    d = lat.desc()
+    _call("lqcd_md_update_links", ctypes.byref(d), _ptr(links), _ptr(mom), float(dt),
+          _stream(stream))
+    return links
+
+
+def pack_links(lat: Lattice, full: torch.Tensor, out: torch.Tensor | None = None,
+               stream=None) -> torch.Tensor:
+    _check(full, lat, (lat.V, 4, 3, 3, 2), "full")
+    out = empty_links(lat, full.device) if out is None else out
+    _check(out, lat, lat.link_shape, "links")
+    d = lat.desc()
+    _call("lqcd_pack_links", ctypes.byref(d), _ptr(full), _ptr(out), _stream(stream))
+    return out
+
+
+def unpack_links(lat: Lattice, links: torch.Tensor, out: torch.Tensor | None = None,
+                 stream=None) -> torch.Tensor:
+    _check(links, lat, lat.link_shape, "links")
+    out = torch.empty((lat.V, 4, 3, 3, 2), dtype=lat.dtype, device=links.device) \
+        if out is None else out
+    _check(out, lat, (lat.V, 4, 3, 3, 2), "full")
+    d = lat.desc()
+    _call("lqcd_unpack_links", ctypes.byref(d), _ptr(links), _ptr(out), _stream(stream))
+    return out
+
+
+# ----------------------------------------------------- layout marshalling
+
+def algebra_to_device(lat: Lattice, a: np.ndarray, device="cuda", pin: bool = False) -> torch.Tensor:
+    """Site-major [V, 4, 8] numpy -> algebra layout tensor (pure reshape)."""
+    W = lat.W
+    soa = np.ascontiguousarray(
+        np.asarray(a).reshape(lat.V, 4, 8 // W, W).transpose(1, 2, 0, 3))
+    t = torch.from_numpy(soa).to(lat.dtype)
+    if pin:
+        t = t.pin_memory()
+    return t.to(device, non_blocking=pin)
+
+
+def algebra_from_device(t: torch.Tensor) -> np.ndarray:
+    """Algebra layout tensor -> site-major float64 numpy [V, 4, 8]."""
+    a = t.detach().to("cpu", torch.float64).numpy()   # [4, 8/W, V, W]
+    V = a.shape[2]
+    return np.ascontiguousarray(a.transpose(2, 0, 1, 3).reshape(V, 4, 8))
+
+
+def full_to_device(lat: Lattice, U: np.ndarray, device="cuda") -> torch.Tensor:
+    """complex [V, 4, 3, 3] numpy -> full tensor [V, 4, 3, 3, 2]."""
+    arr = np.ascontiguousarray(np.asarray(U, dtype=np.complex128)).view(np.float64)
+    return torch.from_numpy(arr.reshape(lat.V, 4, 3, 3, 2)).to(device, lat.dtype)
+
+
+def full_from_device(t: torch.Tensor) -> np.ndarray:
+    """full tensor -> complex128 numpy [V, 4, 3, 3]."""
+    a = t.detach().to("cpu", torch.float64).contiguous().numpy()
+    return a[..., 0] + 1j * a[..., 1]
