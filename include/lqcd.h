@@ -60,6 +60,8 @@ extern "C" {
 #define LQCD_ERR_WORKSPACE (-4)   /* workspace NULL or smaller than required    */
 #define LQCD_ERR_CUDA (-5)        /* a CUDA runtime call or launch failed       */
 #define LQCD_ERR_UNSUPPORTED (-6) /* option not available for this precision    */
+#define LQCD_ERR_CAPACITY (-7)    /* the launch needs more scratch than the
+                                     library's fixed device buffer holds        */
 
 /* Precision of every real in every buffer passed with a descriptor. */
 #define LQCD_F32 0
@@ -121,6 +123,32 @@ int lqcd_gauge_force_update_momenta(const lqcd_desc *desc, const void *links, vo
  * partial sums. */
 int lqcd_gauge_action(const lqcd_desc *desc, const void *links, double *action, void *workspace,
                       size_t workspace_bytes, void *stream);
+
+/* Allocation-free form of lqcd_gauge_action, for callers that cannot
+ * allocate device memory at all: for example a host application that owns
+ * every byte of device memory through its own pool and hands a plug-in only
+ * the buffers it computes on, or a loop with a fixed memory budget where an
+ * extra cudaMalloc (which may also synchronise the device) is not allowed.
+ * The paper has no counterpart; it is an interface convenience.
+ *
+ * Same result as lqcd_gauge_action (the same kernels and the same number of
+ * per-block partial sums, so the value is bitwise identical), but the
+ * partial sums go to a scratch array of 4096 doubles (32 KiB) that the
+ * library keeps in device memory as a file-scope variable; every device
+ * that loads the library holds it until the process exits.  The entry point
+ * calls no cudaMalloc, cudaFree or allocating library routine.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current) and caches it; make
+ *     that first call before any stream capture.
+ *   - All calls share the one array.  Every call overwrites the partial sums
+ *     it reads, so nothing has to be cleared between calls, but two calls
+ *     that overlap on the GPU (different streams, or different host threads
+ *     without ordering) race on it and may both return wrong values.
+ *   - A device whose reduction grid needs more than 4096 partial sums (more
+ *     than 1024 SMs) is rejected with LQCD_ERR_CAPACITY.
+ * links: link layout (device, read); action: one double in device memory. */
+int lqcd_gauge_action_noalloc(const lqcd_desc *desc, const void *links, double *action,
+                              void *stream);
 
 /* Kinetic term K = (1/2) sum_{links, a} p^a p^a of the MD Hamiltonian, in
  * double, same reduction as lqcd_gauge_action.  mom: algebra layout (read);

@@ -5,6 +5,7 @@
 // write one partial each to the caller's workspace, and one block adds the
 // partials in a fixed order.  The grid is a fixed multiple of the SM count,
 // so the summation order -- and the result, bit for bit -- is reproducible.
+#include <cmath>
 #include <mutex>
 
 #include "kernels.h"
@@ -98,6 +99,12 @@ __global__ void __launch_bounds__(kBlock) finish_sum(const double *partials, int
     if (threadIdx.x == 0) *out = scale * s;
 }
 
+// Library-held scratch of the allocation-free action entry point: one double
+// per reduction block.  4096 doubles = 32 KiB, held by every device that
+// loads the library until the process exits.
+constexpr int kFixedPartials = 4096;
+static __device__ __align__(256) double g_fixed_partials[kFixedPartials];
+
 } // namespace
 
 int reduction_blocks(int device)
@@ -173,4 +180,71 @@ const LoopTable &loop_table()
     return tab;
 }
 
+namespace {
+
+// Device address of g_fixed_partials on `device`, looked up once per device
+// (the device must be current).  Host code cannot use the symbol itself: on
+// the host it names a host-side stand-in, not device memory.
+int fixed_partials_address(int device, double **out)
+{
+    static std::mutex mu;
+    static double *addr[64] = {nullptr};
+    if (device < 0 || device >= 64) return LQCD_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(mu);
+    if (addr[device] == nullptr) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_fixed_partials);
+        if (e != cudaSuccess || p == nullptr) return LQCD_ERR_CUDA;
+        addr[device] = static_cast<double *>(p);
+    }
+    *out = addr[device];
+    return LQCD_OK;
+}
+
+} // namespace
+
 } // namespace lqcd
+
+// Allocation-free variant of lqcd_gauge_action (declared in include/lqcd.h):
+// the same kernels, with the per-block partial sums kept in the fixed
+// library-held array above instead of a caller workspace.
+extern "C" int lqcd_gauge_action_noalloc(const lqcd_desc *desc, const void *links, double *action,
+                                         void *stream)
+{
+    if (desc == nullptr || links == nullptr || action == nullptr) return LQCD_ERR_ARG;
+    if (desc->precision != LQCD_F32 && desc->precision != LQCD_F64) return LQCD_ERR_ARG;
+    if (!std::isfinite(desc->beta) || !std::isfinite(desc->c_plaq) ||
+        !std::isfinite(desc->c_rect) || !std::isfinite(desc->c_cube))
+        return LQCD_ERR_ARG;
+    const int64_t limit = ((int64_t)1 << 62) / 72;
+    int64_t V = 1;
+    for (int i = 0; i < 4; ++i) {
+        if (desc->dims[i] < 1) return LQCD_ERR_DIMS;
+        V *= desc->dims[i];
+        if (V > limit) return LQCD_ERR_DIMS;
+    }
+    if (((uintptr_t)links & 15u) != 0) return LQCD_ERR_ALIGN;
+    if (((uintptr_t)action & 7u) != 0) return LQCD_ERR_ALIGN;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LQCD_ERR_CUDA;
+    const int blocks = lqcd::reduction_blocks(dev);
+    if (blocks <= 0) return LQCD_ERR_CUDA;
+    if (blocks > lqcd::kFixedPartials) return LQCD_ERR_CAPACITY;
+    double *partials = nullptr;
+    const int st = lqcd::fixed_partials_address(dev, &partials);
+    if (st != LQCD_OK) return st;
+    lqcd::ReduceArgs a{};
+    for (int i = 0; i < 4; ++i) a.dims[i] = desc->dims[i];
+    a.precision = desc->precision;
+    a.links = links;
+    a.c[0] = desc->c_plaq;
+    a.c[1] = desc->c_rect;
+    a.c[2] = desc->c_cube;
+    a.scale = desc->beta / 3.0;
+    a.partials = partials;
+    a.blocks = blocks;
+    a.out = action;
+    return lqcd::launch_action(a, static_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? LQCD_OK
+               : LQCD_ERR_CUDA;
+}

@@ -262,6 +262,7 @@ const char *lqcd_strerror(int status)
     case LQCD_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
     case LQCD_ERR_CUDA: return "CUDA runtime error";
     case LQCD_ERR_UNSUPPORTED: return "unsupported option";
+    case LQCD_ERR_CAPACITY: return "problem needs more scratch than the fixed library buffer holds";
     default: return "unknown status";
     }
 }

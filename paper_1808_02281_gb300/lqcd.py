@@ -53,6 +53,8 @@ _EXPORTS = {
                                                        ctypes.c_double, ctypes.c_void_p]),
     "lqcd_gauge_action": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_size_t, ctypes.c_void_p]),
+    "lqcd_gauge_action_noalloc": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_void_p]),
     "lqcd_kinetic_energy": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_size_t, ctypes.c_void_p]),
     "lqcd_md_update_momenta": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p,

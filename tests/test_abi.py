@@ -108,7 +108,7 @@ def test_pointer_checks(lib):
 
 def test_strerror(lib):
     assert lib.lqcd_strerror(0) == b"success"
-    for code in range(-6, 0):
+    for code in range(-7, 0):
         assert lib.lqcd_strerror(code) not in (b"", b"unknown status")
     assert lib.lqcd_strerror(-99) == b"unknown status"
     assert lib.lqcd_version() == 1
