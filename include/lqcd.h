@@ -68,12 +68,17 @@ extern "C" {
 #define LQCD_F64 1
 
 /* Force algorithms (lqcd_desc.force_algo). */
-#define LQCD_FORCE_AUTO 0     /* fastest available (currently FACTORED)         */
+#define LQCD_FORCE_AUTO 0     /* STAPLE_FIELDS when the call gets a large enough
+                                 workspace, else FACTORED                       */
 #define LQCD_FORCE_PATHS 1    /* one thread per link walks the 48 staples of a
                                  per-direction path table (plain form)          */
 #define LQCD_FORCE_FACTORED 2 /* one thread per link, staples regrouped by their
                                  shared end links (134 instead of 180 matrix
                                  products per link)                             */
+#define LQCD_FORCE_STAPLE_FIELDS 3 /* two passes: the 24 plaquette staples of
+                                 every site are stored in the workspace, then
+                                 every staple of a link is built from them (63
+                                 products per link); yields the action too     */
 
 /* Problem descriptor.  beta is the inverse coupling of Eq. 18_6_4_1 and
  * (c_plaq, c_rect, c_cube) are the loop coefficients c_P of Eq. 18_3_27_30;
@@ -104,15 +109,51 @@ int lqcd_links_from_omega(const lqcd_desc *desc, const void *omega, void *links,
 
 /* Gauge force of the Symanzik action for every link (Eq. 18_7_25_2 and the
  * force algorithm of Sec. II): f^a = -dS/domega^a.  links: link layout
- * (device, read); force: algebra layout (device, written).  workspace may be
- * NULL (no algorithm needs one yet; lqcd_workspace_bytes reports 0). */
+ * (device, read); force: algebra layout (device, written).  workspace: device
+ * scratch, 256-byte aligned, of lqcd_workspace_bytes(desc) bytes for
+ * LQCD_FORCE_STAPLE_FIELDS (LQCD_ERR_WORKSPACE if missing or short); the
+ * other algorithms ignore it, and LQCD_FORCE_AUTO uses the staple-field
+ * algorithm only when the workspace is large enough. */
 int lqcd_gauge_force(const lqcd_desc *desc, const void *links, void *force, void *workspace,
                      size_t workspace_bytes, void *stream);
 
 /* The force, fused with the momentum step: p^a += dt f^a, without storing f.
- * links: link layout (read); mom: algebra layout (read and written). */
+ * links: link layout (read); mom: algebra layout (read and written).  Uses a
+ * workspace-free algorithm (AUTO means FACTORED here). */
 int lqcd_gauge_force_update_momenta(const lqcd_desc *desc, const void *links, void *mom,
                                     double dt, void *stream);
+
+/* One force evaluation of an MD step, with optional fused consumers:
+ *   force  != NULL: f written (algebra layout, device);
+ *   mom    != NULL: p^a += dt f^a (algebra layout, read and written);
+ *   action != NULL: S_G of the same links written (one device double, FP64).
+ * At least one of the three must be set.  With LQCD_FORCE_STAPLE_FIELDS (or
+ * AUTO and a large enough workspace) the action is a by-product of the force
+ * pass; otherwise the action kernel of lqcd_gauge_action runs after the force.
+ * workspace: lqcd_workspace_bytes(desc) bytes, 256-byte aligned (required
+ * for the staple-field algorithm and whenever action != NULL). */
+int lqcd_md_force_step(const lqcd_desc *desc, const void *links, void *force, void *mom,
+                       double dt, double *action, void *workspace, size_t workspace_bytes,
+                       void *stream);
+
+/* Schedules of the force kernels.  An algorithm may come in several
+ * variants that compute the same result with a different traversal or
+ * pipelining (LQCD_FORCE_STAPLE_FIELDS / AUTO: 4; the others: 1).  The choice
+ * is process-wide per precision.
+ *   lqcd_force_variant_count: number of variants for desc->force_algo.
+ *   lqcd_get_force_variant / lqcd_set_force_variant: the current choice;
+ *     -1 restores the built-in default.  Not thread-safe against concurrent
+ *     force launches of the same precision.
+ *   lqcd_autotune_force: times every variant `reps` times on these links
+ *     (with the fused action, as in an MD step) and keeps the fastest.  It
+ *     SYNCHRONISES the stream (call it once at set-up).  force: a scratch
+ *     buffer in algebra layout, overwritten; workspace as for the force.
+ *     best: the chosen variant; ms: if not NULL, one mean time per variant. */
+int lqcd_force_variant_count(const lqcd_desc *desc);
+int lqcd_get_force_variant(const lqcd_desc *desc);
+int lqcd_set_force_variant(const lqcd_desc *desc, int variant);
+int lqcd_autotune_force(const lqcd_desc *desc, const void *links, void *force, void *workspace,
+                        size_t workspace_bytes, int reps, void *stream, int *best, float *ms);
 
 /* Gauge action S_G = (beta/3) sum_n sum_{34 loops P} c_P [3 - Re tr P_n]
  * (Eq. 18_6_4_1).  links: link layout (device, read).  action: ONE double in
@@ -176,8 +217,11 @@ int lqcd_md_update_links(const lqcd_desc *desc, void *links, const void *mom, do
 int lqcd_pack_links(const lqcd_desc *desc, const void *full, void *links, void *stream);
 int lqcd_unpack_links(const lqcd_desc *desc, const void *links, void *full, void *stream);
 
-/* Bytes of device workspace that lqcd_gauge_action / lqcd_kinetic_energy
- * need for this descriptor on the current device (0 on a bad descriptor). */
+/* Bytes of device workspace that this descriptor needs on the current
+ * device: the staple planes and action partials of the staple-field force
+ * (force_algo STAPLE_FIELDS or AUTO; 24*12 reals per site plus one double per
+ * 128 links) and the partial sums of lqcd_gauge_action / lqcd_kinetic_energy
+ * (0 on a bad descriptor). */
 size_t lqcd_workspace_bytes(const lqcd_desc *desc);
 
 /* Human-readable text of a status code (static storage). */

@@ -89,14 +89,26 @@ template <typename R> __global__ void __launch_bounds__(kBlock) kinetic_partials
     if (threadIdx.x == 0) a.partials[blockIdx.x] = s;
 }
 
-// One block adds the partials in a fixed order and scales the total.
-__global__ void __launch_bounds__(kBlock) finish_sum(const double *partials, int count,
-                                                     double scale, double *out)
+// One block of 1024 threads adds the partials in a fixed order and scales
+// the total.
+constexpr int kFinish = 1024;
+__global__ void __launch_bounds__(kFinish) finish_sum(const double *partials, int count,
+                                                      double scale, double *out)
 {
+    __shared__ double warp_part[kFinish / 32];
     double v = 0.0;
-    for (int i = threadIdx.x; i < count; i += blockDim.x) v += partials[i];
-    const double s = block_sum(v);
-    if (threadIdx.x == 0) *out = scale * s;
+    for (int i = threadIdx.x; i < count; i += kFinish) v += partials[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) warp_part[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double s = warp_part[lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) *out = scale * s;
+    }
 }
 
 // Library-held scratch of the allocation-free action entry point: one double
@@ -131,7 +143,14 @@ cudaError_t launch_action(const ReduceArgs &a, cudaStream_t st)
         action_partials<float><<<a.blocks, kBlock, 0, st>>>(a, loop_table());
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    finish_sum<<<1, kBlock, 0, st>>>(a.partials, a.blocks, a.scale, a.out);
+    finish_sum<<<1, kFinish, 0, st>>>(a.partials, a.blocks, a.scale, a.out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_sum(const double *partials, int count, double scale, double *out,
+                              cudaStream_t st)
+{
+    finish_sum<<<1, kFinish, 0, st>>>(partials, count, scale, out);
     return cudaGetLastError();
 }
 
@@ -143,7 +162,7 @@ cudaError_t launch_kinetic(const ReduceArgs &a, cudaStream_t st)
         kinetic_partials<float><<<a.blocks, kBlock, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    finish_sum<<<1, kBlock, 0, st>>>(a.partials, a.blocks, 1.0, a.out);
+    finish_sum<<<1, kFinish, 0, st>>>(a.partials, a.blocks, 1.0, a.out);
     return cudaGetLastError();
 }
 

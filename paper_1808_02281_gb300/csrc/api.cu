@@ -23,7 +23,8 @@ int check_desc(const lqcd_desc *d)
 {
     if (d == nullptr) return LQCD_ERR_ARG;
     if (d->precision != LQCD_F32 && d->precision != LQCD_F64) return LQCD_ERR_ARG;
-    if (d->force_algo < LQCD_FORCE_AUTO || d->force_algo > LQCD_FORCE_FACTORED) return LQCD_ERR_ARG;
+    if (d->force_algo < LQCD_FORCE_AUTO || d->force_algo > LQCD_FORCE_STAPLE_FIELDS)
+        return LQCD_ERR_ARG;
     if (!std::isfinite(d->beta) || !std::isfinite(d->c_plaq) || !std::isfinite(d->c_rect) ||
         !std::isfinite(d->c_cube))
         return LQCD_ERR_ARG;
@@ -60,7 +61,7 @@ int reduction_setup(const lqcd_desc *desc, void *workspace, size_t workspace_byt
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_status(e);
     const int b = lqcd::reduction_blocks(dev);
-    if (b <= 0) return cuda_status(cudaGetLastError() == cudaSuccess ? cudaErrorUnknown : cudaGetLastError());
+    if (b <= 0) return LQCD_ERR_CUDA;
     if (workspace == nullptr || ((uintptr_t)workspace & 255u) != 0) return LQCD_ERR_WORKSPACE;
     if (workspace_bytes < (size_t)b * sizeof(double)) return LQCD_ERR_WORKSPACE;
     *blocks = b;
@@ -68,13 +69,38 @@ int reduction_setup(const lqcd_desc *desc, void *workspace, size_t workspace_byt
     return LQCD_OK;
 }
 
-int force_common(const lqcd_desc *desc, const void *links, void *force, void *mom, double dt,
-                 void *stream)
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Workspace of the staple-field force: staple planes, then action partials.
+size_t staple_workspace_bytes(const lqcd_desc *d)
 {
+    return lqcd::staple_field_bytes(d->dims, d->precision) +
+           round256((size_t)lqcd::staple_force_partials(d->dims) * sizeof(double));
+}
+
+bool workspace_fits(const void *ws, size_t have, size_t need)
+{
+    return ws != nullptr && ((uintptr_t)ws & 255u) == 0 && have >= need;
+}
+
+// The force (and its fused consumers) with the algorithm the descriptor and
+// the workspace select.  Arguments are already checked.
+int run_force(const lqcd_desc *desc, const void *links, void *force, void *mom, double dt,
+              double *action, void *workspace, size_t workspace_bytes, void *stream)
+{
+    int algo = desc->force_algo;
+    const bool sf_ok = workspace_fits(workspace, workspace_bytes, staple_workspace_bytes(desc));
+    if (algo == LQCD_FORCE_STAPLE_FIELDS && !sf_ok) return LQCD_ERR_WORKSPACE;
+    if (algo == LQCD_FORCE_AUTO) algo = sf_ok ? LQCD_FORCE_STAPLE_FIELDS : LQCD_FORCE_FACTORED;
+    int red_blocks = 0;
+    if (action != nullptr && algo != LQCD_FORCE_STAPLE_FIELDS) {
+        const int s = reduction_setup(desc, workspace, workspace_bytes, &red_blocks);
+        if (s) return s;
+    }
     lqcd::ForceArgs a{};
     copy_dims(a.dims, desc);
     a.precision = desc->precision;
-    a.algo = desc->force_algo == LQCD_FORCE_AUTO ? LQCD_FORCE_FACTORED : desc->force_algo;
+    a.algo = algo;
     a.beta = desc->beta;
     a.c_plaq = desc->c_plaq;
     a.c_rect = desc->c_rect;
@@ -83,7 +109,28 @@ int force_common(const lqcd_desc *desc, const void *links, void *force, void *mo
     a.force = force;
     a.mom = mom;
     a.dt = dt;
-    return cuda_status(lqcd::launch_force(a, as_stream(stream)));
+    a.variant = -1;
+    if (algo == LQCD_FORCE_STAPLE_FIELDS) {
+        char *ws = static_cast<char *>(workspace);
+        a.staples = ws;
+        a.partials = reinterpret_cast<double *>(ws + lqcd::staple_field_bytes(desc->dims, desc->precision));
+        a.action = action;
+        return cuda_status(lqcd::launch_force_staple_fields(a, as_stream(stream)));
+    }
+    int s = cuda_status(lqcd::launch_force(a, as_stream(stream)));
+    if (s || action == nullptr) return s;
+    lqcd::ReduceArgs r{};
+    copy_dims(r.dims, desc);
+    r.precision = desc->precision;
+    r.links = links;
+    r.c[0] = desc->c_plaq;
+    r.c[1] = desc->c_rect;
+    r.c[2] = desc->c_cube;
+    r.scale = desc->beta / 3.0;
+    r.partials = static_cast<double *>(workspace);
+    r.blocks = red_blocks;
+    r.out = action;
+    return cuda_status(lqcd::launch_action(r, as_stream(stream)));
 }
 
 } // namespace
@@ -119,13 +166,11 @@ int lqcd_links_from_omega(const lqcd_desc *desc, const void *omega, void *links,
 int lqcd_gauge_force(const lqcd_desc *desc, const void *links, void *force, void *workspace,
                      size_t workspace_bytes, void *stream)
 {
-    (void)workspace;
-    (void)workspace_bytes;
     int s = check_desc(desc);
     if (s) return s;
     if ((s = check_ptrs({links, force}))) return s;
     if (links == force) return LQCD_ERR_ARG;
-    return force_common(desc, links, force, nullptr, 0.0, stream);
+    return run_force(desc, links, force, nullptr, 0.0, nullptr, workspace, workspace_bytes, stream);
 }
 
 int lqcd_gauge_force_update_momenta(const lqcd_desc *desc, const void *links, void *mom,
@@ -135,7 +180,105 @@ int lqcd_gauge_force_update_momenta(const lqcd_desc *desc, const void *links, vo
     if (s) return s;
     if ((s = check_ptrs({links, mom}))) return s;
     if (links == mom || !std::isfinite(dt)) return LQCD_ERR_ARG;
-    return force_common(desc, links, nullptr, mom, dt, stream);
+    if (desc->force_algo == LQCD_FORCE_STAPLE_FIELDS) return LQCD_ERR_WORKSPACE;
+    return run_force(desc, links, nullptr, mom, dt, nullptr, nullptr, 0, stream);
+}
+
+int lqcd_md_force_step(const lqcd_desc *desc, const void *links, void *force, void *mom,
+                       double dt, double *action, void *workspace, size_t workspace_bytes,
+                       void *stream)
+{
+    int s = check_desc(desc);
+    if (s) return s;
+    if ((s = check_ptrs({links}))) return s;
+    if (force == nullptr && mom == nullptr && action == nullptr) return LQCD_ERR_ARG;
+    if (force != nullptr && ((s = check_ptrs({force})))) return s;
+    if (mom != nullptr && ((s = check_ptrs({mom})))) return s;
+    if (action != nullptr && ((uintptr_t)action & 7u) != 0) return LQCD_ERR_ALIGN;
+    if (links == force || links == mom || (force != nullptr && force == mom)) return LQCD_ERR_ARG;
+    if (mom != nullptr && !std::isfinite(dt)) return LQCD_ERR_ARG;
+    return run_force(desc, links, force, mom, dt, action, workspace, workspace_bytes, stream);
+}
+
+int lqcd_force_variant_count(const lqcd_desc *desc)
+{
+    const int s = check_desc(desc);
+    if (s) return s;
+    const bool sf = desc->force_algo == LQCD_FORCE_AUTO || desc->force_algo == LQCD_FORCE_STAPLE_FIELDS;
+    return sf ? lqcd::staple_force_variants() : 1;
+}
+
+int lqcd_get_force_variant(const lqcd_desc *desc)
+{
+    const int s = check_desc(desc);
+    if (s) return s;
+    const bool sf = desc->force_algo == LQCD_FORCE_AUTO || desc->force_algo == LQCD_FORCE_STAPLE_FIELDS;
+    return sf ? lqcd::staple_force_variant(desc->precision) : 0;
+}
+
+int lqcd_set_force_variant(const lqcd_desc *desc, int variant)
+{
+    const int s = check_desc(desc);
+    if (s) return s;
+    const bool sf = desc->force_algo == LQCD_FORCE_AUTO || desc->force_algo == LQCD_FORCE_STAPLE_FIELDS;
+    const int count = sf ? lqcd::staple_force_variants() : 1;
+    if (variant < -1 || variant >= count) return LQCD_ERR_ARG;
+    if (sf) lqcd::set_staple_force_variant(desc->precision, variant);
+    return LQCD_OK;
+}
+
+int lqcd_autotune_force(const lqcd_desc *desc, const void *links, void *force, void *workspace,
+                        size_t workspace_bytes, int reps, void *stream, int *best, float *ms)
+{
+    int s = check_desc(desc);
+    if (s) return s;
+    if ((s = check_ptrs({links, force}))) return s;
+    if (links == force || reps < 1) return LQCD_ERR_ARG;
+    const bool sf = desc->force_algo == LQCD_FORCE_AUTO || desc->force_algo == LQCD_FORCE_STAPLE_FIELDS;
+    if (!sf) {
+        if (best) *best = 0;
+        return LQCD_OK;
+    }
+    if (!workspace_fits(workspace, workspace_bytes, staple_workspace_bytes(desc)))
+        return LQCD_ERR_WORKSPACE;
+    lqcd_desc d = *desc;
+    d.force_algo = LQCD_FORCE_STAPLE_FIELDS;
+    double *action = static_cast<double *>(force); // scratch: force[0] receives the action
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    const int count = lqcd::staple_force_variants();
+    int arg = 0;
+    float best_ms = 0.f;
+    for (int v = 0; v < count && ce == cudaSuccess && s == LQCD_OK; ++v) {
+        lqcd::set_staple_force_variant(desc->precision, v);
+        s = run_force(&d, links, force, nullptr, 0.0, action, workspace, workspace_bytes, stream);
+        if (s) break;
+        float acc = 0.f;
+        for (int r = 0; r < reps && s == LQCD_OK && ce == cudaSuccess; ++r) {
+            ce = cudaEventRecord(e0, as_stream(stream));
+            if (ce != cudaSuccess) break;
+            s = run_force(&d, links, force, nullptr, 0.0, action, workspace, workspace_bytes, stream);
+            if (s) break;
+            ce = cudaEventRecord(e1, as_stream(stream));
+            if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+            float t = 0.f;
+            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, e0, e1);
+            acc += t;
+        }
+        const float mean = acc / (float)reps;
+        if (ms) ms[v] = mean;
+        if (v == 0 || mean < best_ms) {
+            best_ms = mean;
+            arg = v;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s == LQCD_OK && ce != cudaSuccess) s = cuda_status(ce);
+    lqcd::set_staple_force_variant(desc->precision, s == LQCD_OK ? arg : -1);
+    if (best) *best = s == LQCD_OK ? arg : -1;
+    return s;
 }
 
 int lqcd_gauge_action(const lqcd_desc *desc, const void *links, double *action, void *workspace,
@@ -249,7 +392,12 @@ size_t lqcd_workspace_bytes(const lqcd_desc *desc)
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     const int b = lqcd::reduction_blocks(dev);
     if (b <= 0) return 0;
-    return ((size_t)b * sizeof(double) + 255) & ~(size_t)255;
+    size_t need = round256((size_t)b * sizeof(double));
+    if (desc->force_algo == LQCD_FORCE_AUTO || desc->force_algo == LQCD_FORCE_STAPLE_FIELDS) {
+        const size_t sf = staple_workspace_bytes(desc);
+        if (sf > need) need = sf;
+    }
+    return need;
 }
 
 const char *lqcd_strerror(int status)

@@ -42,7 +42,7 @@ __device__ __forceinline__ Mat<R> walk(const R *__restrict__ links, const Geom &
 }
 
 // Epilogue shared by both kernels: f = components of (beta/6)(U t)_TA, then
-// either store f or apply the momentum step p += dt f.
+// store f and/or apply the momentum step p += dt f.
 template <typename R>
 __device__ __forceinline__ void finish(const ForceArgs &a, const R *__restrict__ links,
                                        const Geom &g, int rho, int64_t n, const Mat<R> &t)
@@ -51,9 +51,8 @@ __device__ __forceinline__ void finish(const ForceArgs &a, const R *__restrict__
     const Mat<R> m = mul<N, N>(u, t);
     R f[8];
     ta_components(m, R(a.beta / 6.0), f);
-    if (a.mom == nullptr) {
-        store_algebra(static_cast<R *>(a.force), g.V, rho, n, f);
-    } else {
+    if (a.force != nullptr) store_algebra(static_cast<R *>(a.force), g.V, rho, n, f);
+    if (a.mom != nullptr) {
         R *mom = static_cast<R *>(a.mom);
         R p[8];
         load_algebra(mom, g.V, rho, n, p);

@@ -25,6 +25,15 @@ struct StapleTable {
 
 const StapleTable &staple_table();
 
+// Per-launch scalars computed once on the host, in both precisions, so that
+// no kernel thread spends FP64 instructions on them: beta/6, c_plaq, c_rect,
+// c_cube, the per-link action constant 3 (1.5 c_plaq + 3 c_rect + 4 c_cube),
+// c_plaq/12 and dt.
+struct KernelScalars {
+    double d[7];
+    float f[7];
+};
+
 struct ForceArgs {
     int dims[4];
     int precision;
@@ -32,11 +41,27 @@ struct ForceArgs {
     double beta, c_plaq, c_rect, c_cube;
     const void *links;
     void *force; // written when mom == nullptr
-    void *mom;   // when set: mom += dt * f, force not written
+    void *mom;   // when set: mom += dt * f
     double dt;
+    void *staples;     // staple-field algorithm: workspace for the 24 staple planes
+    double *partials;  // staple-field algorithm with action: per-block partial sums
+    double *action;    // staple-field algorithm: action written here when set
+    int sweep[3];      // staple-field force pass: spatial block extents of the traversal
+    int micro[3];      // staple-field force pass: micro-tile extents inside a block slice
+    int variant;       // staple-field force pass schedule; -1 = process-wide choice
+    KernelScalars sc;  // filled by the staple-field launcher
 };
 
 cudaError_t launch_force(const ForceArgs &a, cudaStream_t st);
+
+// Staple-field algorithm (force_sf.cu): workspace bytes of the 24 staple
+// planes, number of per-block action partials, and the two-pass launch.
+size_t staple_field_bytes(const int dims[4], int precision);
+int staple_force_partials(const int dims[4]);
+cudaError_t launch_force_staple_fields(const ForceArgs &a, cudaStream_t st);
+int staple_force_variants();
+int staple_force_variant(int precision);
+void set_staple_force_variant(int precision, int variant);
 
 // The 34 loops of the action kernel: cls, len (4 or 6), signed directions.
 struct Loop {
@@ -65,6 +90,9 @@ struct ReduceArgs {
 };
 
 int reduction_blocks(int device);
+// out = scale * (sum of partials[0..count)), one block, fixed order.
+cudaError_t launch_finish_sum(const double *partials, int count, double scale, double *out,
+                              cudaStream_t st);
 cudaError_t launch_action(const ReduceArgs &a, cudaStream_t st);
 cudaError_t launch_kinetic(const ReduceArgs &a, cudaStream_t st);
 

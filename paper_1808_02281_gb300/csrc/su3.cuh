@@ -100,6 +100,45 @@ __device__ __forceinline__ Mat<R> mul(const Mat<R> &a, const Mat<R> &b)
     return c;
 }
 
+// Rows 0 and 1 of op_a(a) * op_b(b) (row 2 left zero): enough for a product
+// that is stored in the compact two-row form.
+template <int FA, int FB, typename R>
+__device__ __forceinline__ Mat<R> mul_top2(const Mat<R> &a, const Mat<R> &b)
+{
+    Mat<R> c;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            if (i == 2) {
+                c.re[i][j] = c.im[i][j] = R(0);
+                continue;
+            }
+            R re = R(0), im = R(0);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                re = fma(el_re<FA>(a, i, k), el_re<FB>(b, k, j), re);
+                re = fma(-el_im<FA>(a, i, k), el_im<FB>(b, k, j), re);
+                im = fma(el_re<FA>(a, i, k), el_im<FB>(b, k, j), im);
+                im = fma(el_im<FA>(a, i, k), el_re<FB>(b, k, j), im);
+            }
+            c.re[i][j] = re;
+            c.im[i][j] = im;
+        }
+    return c;
+}
+
+template <typename R> __device__ __forceinline__ void add_to(Mat<R> &c, const Mat<R> &a)
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            c.re[i][j] += a.re[i][j];
+            c.im[i][j] += a.im[i][j];
+        }
+}
+
 // c += op_a(a) * op_b(b)   (the accumulation is free: every term is an FMA)
 template <int FA, int FB, typename R>
 __device__ __forceinline__ void mul_acc(Mat<R> &c, const Mat<R> &a, const Mat<R> &b)

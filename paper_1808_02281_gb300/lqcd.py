@@ -24,7 +24,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblqcd.so")
 
 F32, F64 = 0, 1
-FORCE_AUTO, FORCE_PATHS, FORCE_FACTORED = 0, 1, 2
+FORCE_AUTO, FORCE_PATHS, FORCE_FACTORED, FORCE_STAPLE_FIELDS = 0, 1, 2, 3
 
 
 class LqcdError(RuntimeError):
@@ -51,6 +51,9 @@ _EXPORTS = {
                                         ctypes.c_size_t, ctypes.c_void_p]),
     "lqcd_gauge_force_update_momenta": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p,
                                                        ctypes.c_double, ctypes.c_void_p]),
+    "lqcd_md_force_step": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                          ctypes.c_void_p]),
     "lqcd_gauge_action": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_size_t, ctypes.c_void_p]),
     "lqcd_gauge_action_noalloc": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p,
@@ -64,6 +67,12 @@ _EXPORTS = {
     "lqcd_pack_links": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "lqcd_unpack_links": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "lqcd_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(Desc)]),
+    "lqcd_force_variant_count": (ctypes.c_int, [ctypes.POINTER(Desc)]),
+    "lqcd_get_force_variant": (ctypes.c_int, [ctypes.POINTER(Desc)]),
+    "lqcd_set_force_variant": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_int]),
+    "lqcd_autotune_force": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p,
+                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
     "lqcd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "lqcd_last_cuda_error": (ctypes.c_int, []),
     "lqcd_version": (ctypes.c_int, []),
@@ -205,14 +214,46 @@ def links_from_omega(lat: Lattice, omega: torch.Tensor, out: torch.Tensor | None
 
 
 def gauge_force(lat: Lattice, links: torch.Tensor, out: torch.Tensor | None = None,
-                stream=None) -> torch.Tensor:
-    """f^a = -dS/domega^a for every link (algebra layout)."""
+                workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """f^a = -dS/domega^a for every link (algebra layout).  Without a
+    workspace one is allocated for the algorithms that use it."""
     _check(links, lat, lat.link_shape, "links")
     out = empty_algebra(lat, links.device) if out is None else out
     _check(out, lat, lat.algebra_shape, "force")
+    ws = _workspace_for(lat, links.device, workspace)
     d = lat.desc()
-    _call("lqcd_gauge_force", ctypes.byref(d), _ptr(links), _ptr(out), None, 0, _stream(stream))
+    _call("lqcd_gauge_force", ctypes.byref(d), _ptr(links), _ptr(out),
+          None if ws is None else _ptr(ws), 0 if ws is None else ws.numel(), _stream(stream))
     return out
+
+
+def md_force_step(lat: Lattice, links: torch.Tensor, force: torch.Tensor | None = None,
+                  mom: torch.Tensor | None = None, dt: float = 0.0,
+                  action: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                  stream=None):
+    """One force evaluation with optional fused consumers: store f, apply
+    p += dt f, and/or write S_G (0-d float64 device tensor)."""
+    _check(links, lat, lat.link_shape, "links")
+    if force is not None:
+        _check(force, lat, lat.algebra_shape, "force")
+    if mom is not None:
+        _check(mom, lat, lat.algebra_shape, "mom")
+    if action is not None and (action.dtype != torch.float64 or not action.is_cuda):
+        raise TypeError("action must be a float64 CUDA tensor")
+    ws = make_workspace(lat, links.device) if workspace is None else workspace
+    d = lat.desc()
+    p = lambda t: None if t is None else _ptr(t)
+    _call("lqcd_md_force_step", ctypes.byref(d), _ptr(links), p(force), p(mom), float(dt),
+          p(action), _ptr(ws), ws.numel(), _stream(stream))
+    return force, mom, action
+
+
+def _workspace_for(lat: Lattice, device, workspace):
+    if workspace is not None:
+        return workspace
+    if lat.force_algo in (FORCE_AUTO, FORCE_STAPLE_FIELDS):
+        return make_workspace(lat, device)
+    return None
 
 
 def gauge_force_update_momenta(lat: Lattice, links: torch.Tensor, mom: torch.Tensor, dt: float,
@@ -289,6 +330,40 @@ def unpack_links(lat: Lattice, links: torch.Tensor, out: torch.Tensor | None = N
     d = lat.desc()
     _call("lqcd_unpack_links", ctypes.byref(d), _ptr(links), _ptr(out), _stream(stream))
     return out
+
+
+def force_variant_count(lat: Lattice) -> int:
+    d = lat.desc()
+    n = _lib().lqcd_force_variant_count(ctypes.byref(d))
+    if n < 0:
+        raise LqcdError(n, "lqcd_force_variant_count")
+    return n
+
+
+def get_force_variant(lat: Lattice) -> int:
+    d = lat.desc()
+    return int(_lib().lqcd_get_force_variant(ctypes.byref(d)))
+
+
+def set_force_variant(lat: Lattice, variant: int) -> None:
+    d = lat.desc()
+    _call("lqcd_set_force_variant", ctypes.byref(d), int(variant))
+
+
+def autotune_force(lat: Lattice, links: torch.Tensor, reps: int = 3,
+                   workspace: torch.Tensor | None = None, stream=None):
+    """Time every force variant on these links and keep the fastest (the
+    stream is synchronised).  Returns (best variant, [mean ms per variant])."""
+    _check(links, lat, lat.link_shape, "links")
+    n = force_variant_count(lat)
+    scratch = empty_algebra(lat, links.device)
+    ws = make_workspace(lat, links.device) if workspace is None else workspace
+    best = ctypes.c_int(-1)
+    ms = (ctypes.c_float * n)()
+    d = lat.desc()
+    _call("lqcd_autotune_force", ctypes.byref(d), _ptr(links), _ptr(scratch), _ptr(ws), ws.numel(),
+          int(reps), _stream(stream), ctypes.byref(best), ms)
+    return best.value, [ms[i] for i in range(n)]
 
 
 # ----------------------------------------------------- layout marshalling

@@ -79,7 +79,10 @@ def test_links_from_omega(dims, sigma, u0, prec):
     assert np.abs(U - ref["U"]).max() < TOL_U[prec]
 
 
-@pytest.mark.parametrize("algo", [lqcd.FORCE_PATHS, lqcd.FORCE_FACTORED])
+ALGOS = [lqcd.FORCE_PATHS, lqcd.FORCE_FACTORED, lqcd.FORCE_STAPLE_FIELDS]
+
+
+@pytest.mark.parametrize("algo", ALGOS)
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("dims,sigma,u0", CASES)
 def test_force_parity(dims, sigma, u0, prec, algo):
@@ -161,6 +164,80 @@ def test_md_updates_parity(prec):
     K = float(lqcd.kinetic_energy(lat, lqcd.algebra_to_device(lat, p)).item())
     tolk = 1e-13 if prec == "f64" else 1e-6
     assert abs(K - O.kinetic_energy(p)) <= tolk * O.kinetic_energy(p)
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("dims,sigma,u0", CASES)
+def test_md_force_step_parity(dims, sigma, u0, prec, algo):
+    """Force, fused momentum step and action from one call, against the
+    oracle's force, momentum step and action."""
+    ref = oracle_case(dims, sigma, u0, 0)
+    lat = lqcd.Lattice.symanzik(dims, 6.0, u0, prec, force_algo=algo)
+    U = gpu_links(lat, ref["omega"])
+    p = synth.momenta(dims, seed=4)
+    mom = lqcd.algebra_to_device(lat, p)
+    force = lqcd.empty_algebra(lat)
+    S = torch.empty((), dtype=torch.float64, device="cuda")
+    lqcd.md_force_step(lat, U, force=force, mom=mom, dt=0.05, action=S)
+    assert rel_force_err(lqcd.algebra_from_device(force), ref["f"]) <= TOL_F[prec]
+    assert abs(float(S.item()) - ref["S"]) <= TOL_S[prec] * abs(ref["S"])
+    p_ref = O.md_update_momenta(p, ref["f"], 0.05)
+    tolp = 1e-12 if prec == "f64" else 2e-5
+    assert np.abs(lqcd.algebra_from_device(mom) - p_ref).max() <= tolp * np.abs(p_ref).max()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("dims,sigma,u0", CASES)
+def test_staple_field_variants_parity(dims, sigma, u0, prec):
+    """Every schedule of the staple-field force gives the oracle's force and
+    action (odd and degenerate extents included)."""
+    ref = oracle_case(dims, sigma, u0, 0)
+    lat = lqcd.Lattice.symanzik(dims, 6.0, u0, prec, force_algo=lqcd.FORCE_STAPLE_FIELDS)
+    U = gpu_links(lat, ref["omega"])
+    try:
+        for v in range(lqcd.force_variant_count(lat)):
+            lqcd.set_force_variant(lat, v)
+            assert lqcd.get_force_variant(lat) == v
+            force = lqcd.empty_algebra(lat)
+            S = torch.empty((), dtype=torch.float64, device="cuda")
+            lqcd.md_force_step(lat, U, force=force, action=S)
+            assert rel_force_err(lqcd.algebra_from_device(force), ref["f"]) <= TOL_F[prec], v
+            assert abs(float(S.item()) - ref["S"]) <= TOL_S[prec] * abs(ref["S"]), v
+    finally:
+        lqcd.set_force_variant(lat, -1)
+
+
+def test_autotune_force():
+    dims = (8, 8, 8, 16)
+    lat = lqcd.Lattice.symanzik(dims, 6.0, 0.87, "f32", force_algo=lqcd.FORCE_STAPLE_FIELDS)
+    U = gpu_links(lat, synth.omega(dims, 0.3, 0))
+    try:
+        best, ms = lqcd.autotune_force(lat, U, reps=2)
+        assert 0 <= best < lqcd.force_variant_count(lat) == len(ms)
+        assert all(t > 0 for t in ms) and ms[best] == min(ms)
+        assert lqcd.get_force_variant(lat) == best
+        with pytest.raises(lqcd.LqcdError):
+            lqcd.set_force_variant(lat, len(ms))
+    finally:
+        lqcd.set_force_variant(lat, -1)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_staple_field_workspace_contract(prec):
+    """STAPLE_FIELDS without a large enough workspace is an error; AUTO falls
+    back to a workspace-free algorithm and gives the same force."""
+    dims = (4, 4, 4, 6)
+    lat = lqcd.Lattice.symanzik(dims, 6.0, 0.87, prec, force_algo=lqcd.FORCE_STAPLE_FIELDS)
+    U = gpu_links(lat, synth.omega(dims, 0.3, 0))
+    small = torch.empty(256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(lqcd.LqcdError) as e:
+        lqcd.gauge_force(lat, U, workspace=small)
+    assert e.value.status == -4
+    f_sf = lqcd.algebra_from_device(lqcd.gauge_force(lat, U))
+    auto = lat.with_(force_algo=lqcd.FORCE_AUTO)
+    f_auto_small = lqcd.algebra_from_device(lqcd.gauge_force(auto, U, workspace=small))
+    assert rel_force_err(f_auto_small, f_sf) <= TOL_F[prec]
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
@@ -251,8 +328,13 @@ def test_force_sampled_full_size(prec):
     U = gpu_links(lat, synth.omega(dims, w["sigma"], w["seed"]))
     f = lqcd.gauge_force(lat, U)
     fa = lqcd.algebra_from_device(f)
-    del U, f
+    f2 = lqcd.gauge_force(lat.with_(force_algo=lqcd.FORCE_FACTORED), U)
+    fb = lqcd.algebra_from_device(f2)
+    del U, f, f2
     got = fa.reshape(-1, 8)[links]
     want = _sampled_oracle(dims, w["sigma"], w["u0"], links)
     assert rel_force_err(got, want) <= TOL_F[prec]
+    assert rel_force_err(fb.reshape(-1, 8)[links], want) <= TOL_F[prec]
     assert np.isfinite(fa).all()
+    # every link: the two algorithms agree within twice the tolerance
+    assert rel_force_err(fa, fb) <= 2 * TOL_F[prec]
