@@ -332,6 +332,35 @@ def run_ours(args):
     del U, mom, force, S, ws
     e2e_value = world * nlinks * K_e2e / (e_ms / 1e3) / 1e9
 
+    # dH of one Omelyan trajectory (tau 0.5, dt 0.05) from the same draws in
+    # FP32 and FP64, H = K + S in FP64 (FP64 action of the FP32-stored links)
+    from paper_1808_02281_gb300 import hmc
+    dh = {"integrator": "omelyan", "tau": 0.5, "dt": 0.05, "dims": list(dims)}
+    for prec in ("f32", "f64"):
+        st = hmc.initial_state(dims, prec, w["sigma"], w["u0"], w["beta"], w["seed"] + rank)
+        dh[prec] = hmc.trajectory(st, 0.5, 0.05, "omelyan", action_precision="f64")
+        del st
+        torch.cuda.empty_cache()
+    dh["abs_err_f32"] = abs(dh["f32"] - dh["f64"])
+    # the same FP32 trajectory captured as one CUDA graph, replayed
+    st = hmc.initial_state(dims, "f32", w["sigma"], w["u0"], w["beta"], w["seed"] + rank)
+    g_traj = hmc.GraphTrajectory(st, 0.05, 10, "omelyan")
+    g_traj.replay()
+    torch.cuda.synchronize(dev)
+    t_start, t_stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    g_traj.replay()
+    t_stop.record(stream)
+    torch.cuda.synchronize(dev)
+    dh["trajectory_graph_ms"] = t_start.elapsed_time(t_stop)
+    t_start.record(stream)
+    hmc.omelyan(st, 0.05, 10)
+    t_stop.record(stream)
+    torch.cuda.synchronize(dev)
+    dh["trajectory_eager_ms"] = t_start.elapsed_time(t_stop)
+    del st, g_traj
+    torch.cuda.empty_cache()
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -385,6 +414,7 @@ def run_ours(args):
                 "ms_per_step": ms64 / k64, "force_ms": per64["force"],
                 "force_glinks": nlinks / (per64["force"] / 1e3) / 1e9, "steps": k64},
         "action_f32": S32, "action_f64": S64,
+        "dH": dh,
         "roofline": roofline,
         "streaming": streaming,
         "cpu_baseline": cpu,

@@ -50,6 +50,12 @@
 extern "C" {
 #endif
 
+#if defined(__GNUC__)
+#define LQCD_API __attribute__((visibility("default")))
+#else
+#define LQCD_API
+#endif
+
 #define LQCD_VERSION 1
 
 /* Status codes. */
@@ -98,14 +104,14 @@ typedef struct lqcd_desc {
  *   c_rect = -(1 + 0.4805 alpha_s) / (20 u0^2),
  *   c_cube = -2 * 0.03325 alpha_s / u0^2   (the printed factor 2 is kept).
  * u0 must be finite and > 0.  Any output pointer may be NULL. */
-int lqcd_symanzik_coefficients(double u0, double *alpha_s, double *c_plaq, double *c_rect,
+LQCD_API int lqcd_symanzik_coefficients(double u0, double *alpha_s, double *c_plaq, double *c_rect,
                                double *c_cube);
 
 /* Links from their algebra parameters, U_{n,mu} = exp(i sum_a omega^a T_a)
  * (Eq. 18_1_29_3).  omega: algebra layout (device, read); links: link layout
  * (device, written).  The exponential is the Cayley-Hamilton form
  * f0 + f1 Q + f2 Q^2 (exact for 3x3), coefficients by their power series. */
-int lqcd_links_from_omega(const lqcd_desc *desc, const void *omega, void *links, void *stream);
+LQCD_API int lqcd_links_from_omega(const lqcd_desc *desc, const void *omega, void *links, void *stream);
 
 /* Gauge force of the Symanzik action for every link (Eq. 18_7_25_2 and the
  * force algorithm of Sec. II): f^a = -dS/domega^a.  links: link layout
@@ -114,13 +120,13 @@ int lqcd_links_from_omega(const lqcd_desc *desc, const void *omega, void *links,
  * LQCD_FORCE_STAPLE_FIELDS (LQCD_ERR_WORKSPACE if missing or short); the
  * other algorithms ignore it, and LQCD_FORCE_AUTO uses the staple-field
  * algorithm only when the workspace is large enough. */
-int lqcd_gauge_force(const lqcd_desc *desc, const void *links, void *force, void *workspace,
+LQCD_API int lqcd_gauge_force(const lqcd_desc *desc, const void *links, void *force, void *workspace,
                      size_t workspace_bytes, void *stream);
 
 /* The force, fused with the momentum step: p^a += dt f^a, without storing f.
  * links: link layout (read); mom: algebra layout (read and written).  Uses a
  * workspace-free algorithm (AUTO means FACTORED here). */
-int lqcd_gauge_force_update_momenta(const lqcd_desc *desc, const void *links, void *mom,
+LQCD_API int lqcd_gauge_force_update_momenta(const lqcd_desc *desc, const void *links, void *mom,
                                     double dt, void *stream);
 
 /* One force evaluation of an MD step, with optional fused consumers:
@@ -132,7 +138,7 @@ int lqcd_gauge_force_update_momenta(const lqcd_desc *desc, const void *links, vo
  * pass; otherwise the action kernel of lqcd_gauge_action runs after the force.
  * workspace: lqcd_workspace_bytes(desc) bytes, 256-byte aligned (required
  * for the staple-field algorithm and whenever action != NULL). */
-int lqcd_md_force_step(const lqcd_desc *desc, const void *links, void *force, void *mom,
+LQCD_API int lqcd_md_force_step(const lqcd_desc *desc, const void *links, void *force, void *mom,
                        double dt, double *action, void *workspace, size_t workspace_bytes,
                        void *stream);
 
@@ -149,10 +155,10 @@ int lqcd_md_force_step(const lqcd_desc *desc, const void *links, void *force, vo
  *     SYNCHRONISES the stream (call it once at set-up).  force: a scratch
  *     buffer in algebra layout, overwritten; workspace as for the force.
  *     best: the chosen variant; ms: if not NULL, one mean time per variant. */
-int lqcd_force_variant_count(const lqcd_desc *desc);
-int lqcd_get_force_variant(const lqcd_desc *desc);
-int lqcd_set_force_variant(const lqcd_desc *desc, int variant);
-int lqcd_autotune_force(const lqcd_desc *desc, const void *links, void *force, void *workspace,
+LQCD_API int lqcd_force_variant_count(const lqcd_desc *desc);
+LQCD_API int lqcd_get_force_variant(const lqcd_desc *desc);
+LQCD_API int lqcd_set_force_variant(const lqcd_desc *desc, int variant);
+LQCD_API int lqcd_autotune_force(const lqcd_desc *desc, const void *links, void *force, void *workspace,
                         size_t workspace_bytes, int reps, void *stream, int *best, float *ms);
 
 /* Gauge action S_G = (beta/3) sum_n sum_{34 loops P} c_P [3 - Re tr P_n]
@@ -162,7 +168,7 @@ int lqcd_autotune_force(const lqcd_desc *desc, const void *links, void *force, v
  * bitwise reproducible).  workspace: device scratch of at least
  * lqcd_workspace_bytes(desc) bytes, 256-byte aligned, used for per-block
  * partial sums. */
-int lqcd_gauge_action(const lqcd_desc *desc, const void *links, double *action, void *workspace,
+LQCD_API int lqcd_gauge_action(const lqcd_desc *desc, const void *links, double *action, void *workspace,
                       size_t workspace_bytes, void *stream);
 
 /* Allocation-free form of lqcd_gauge_action, for callers that cannot
@@ -188,50 +194,70 @@ int lqcd_gauge_action(const lqcd_desc *desc, const void *links, double *action, 
  *   - A device whose reduction grid needs more than 4096 partial sums (more
  *     than 1024 SMs) is rejected with LQCD_ERR_CAPACITY.
  * links: link layout (device, read); action: one double in device memory. */
-int lqcd_gauge_action_noalloc(const lqcd_desc *desc, const void *links, double *action,
+LQCD_API int lqcd_gauge_action_noalloc(const lqcd_desc *desc, const void *links, double *action,
                               void *stream);
 
 /* Kinetic term K = (1/2) sum_{links, a} p^a p^a of the MD Hamiltonian, in
  * double, same reduction as lqcd_gauge_action.  mom: algebra layout (read);
  * energy: one double in device memory (written). */
-int lqcd_kinetic_energy(const lqcd_desc *desc, const void *mom, double *energy, void *workspace,
+LQCD_API int lqcd_kinetic_energy(const lqcd_desc *desc, const void *mom, double *energy, void *workspace,
                         size_t workspace_bytes, void *stream);
 
 /* Momentum step p^a += dt f^a for every link (the equation of motion of
  * H = K + S_G with f = -dS/domega, Eq. 18_7_25_1).  mom: algebra layout (read
  * and written); force: algebra layout (read).  mom == force is rejected. */
-int lqcd_md_update_momenta(const lqcd_desc *desc, void *mom, const void *force, double dt,
+LQCD_API int lqcd_md_update_momenta(const lqcd_desc *desc, void *mom, const void *force, double dt,
                            void *stream);
 
 /* Link step U <- exp(i dt sum_a p^a T_a) U for every link (the flow of the
  * left parametrisation of Eq. 18_1_29_3), then Gram-Schmidt of rows 0, 1
  * (row 2 is always rebuilt as conj(row0 x row1)).  links: link layout (read
  * and written); mom: algebra layout (read). */
-int lqcd_md_update_links(const lqcd_desc *desc, void *links, const void *mom, double dt,
+LQCD_API int lqcd_md_update_links(const lqcd_desc *desc, void *links, const void *mom, double dt,
                          void *stream);
+
+/* Gradient of S with respect to the algebra parameters of the links,
+ * for S as a function of omega through U = exp(i omega.T) U0 (Eq. 18_1_29_3):
+ *   grad^a = dS/domega^a = components of phi(-ad_X)(-i f.T),  X = i omega.T,
+ * phi(z) = (e^z - 1)/z, where f is the force of lqcd_gauge_force evaluated at
+ * U (the left derivative of Eqs. 18_7_25_1, 18_7_26_1).  At omega = 0 this is
+ * -f.  omega, force: algebra layout (read); grad: algebra layout (written). */
+LQCD_API int lqcd_omega_gradient(const lqcd_desc *desc, const void *omega, const void *force, void *grad,
+                        void *stream);
+
+/* Precision conversion of a link field (lqcd_convert_links, 12 stored reals
+ * per link) or an algebra field (lqcd_convert_algebra, 8 per link) from
+ * desc->precision to dst_precision, value by value (FP32 -> FP64 is exact;
+ * FP64 -> FP32 rounds to nearest).  Used to evaluate FP32-stored links with
+ * FP64 arithmetic (the Metropolis action of an FP32 trajectory).
+ * src, dst: device, the two layouts of the two precisions; src != dst. */
+LQCD_API int lqcd_convert_links(const lqcd_desc *desc, const void *src, int dst_precision,
+                                void *dst, void *stream);
+LQCD_API int lqcd_convert_algebra(const lqcd_desc *desc, const void *src, int dst_precision,
+                                  void *dst, void *stream);
 
 /* Layout conversions between full complex 3x3 links ([V][4][3][3] (re, im))
  * and the compact link layout, in the descriptor's precision.  pack drops
  * row 2 (the input must be SU(3) for the result to mean the same links);
  * unpack rebuilds it. */
-int lqcd_pack_links(const lqcd_desc *desc, const void *full, void *links, void *stream);
-int lqcd_unpack_links(const lqcd_desc *desc, const void *links, void *full, void *stream);
+LQCD_API int lqcd_pack_links(const lqcd_desc *desc, const void *full, void *links, void *stream);
+LQCD_API int lqcd_unpack_links(const lqcd_desc *desc, const void *links, void *full, void *stream);
 
 /* Bytes of device workspace that this descriptor needs on the current
  * device: the staple planes and action partials of the staple-field force
  * (force_algo STAPLE_FIELDS or AUTO; 24*12 reals per site plus one double per
  * 128 links) and the partial sums of lqcd_gauge_action / lqcd_kinetic_energy
  * (0 on a bad descriptor). */
-size_t lqcd_workspace_bytes(const lqcd_desc *desc);
+LQCD_API size_t lqcd_workspace_bytes(const lqcd_desc *desc);
 
 /* Human-readable text of a status code (static storage). */
-const char *lqcd_strerror(int status);
+LQCD_API const char *lqcd_strerror(int status);
 
 /* The last CUDA error code seen by this library on the calling thread. */
-int lqcd_last_cuda_error(void);
+LQCD_API int lqcd_last_cuda_error(void);
 
 /* LQCD_VERSION of the built library. */
-int lqcd_version(void);
+LQCD_API int lqcd_version(void);
 
 #ifdef __cplusplus
 }

@@ -228,5 +228,23 @@ def leapfrog(dims, U, p, beta: float, c, dt: float, nsteps: int):
     return U, p
 
 
+OMELYAN_LAMBDA = 0.1931833275037836
+
+
+def omelyan(dims, U, p, beta: float, c, dt: float, nsteps: int, lam: float = OMELYAN_LAMBDA):
+    """Second-order minimum-norm integrator (Omelyan, Mryglod & Folk 2003)
+    built from the oracle's MD steps: per step p(l dt) U(dt/2) p((1-2l) dt)
+    U(dt/2) p(l dt), the last kick of a step merged with the first of the
+    next.  (The paper names no integrator; this one is a test reference.)"""
+    p = md_update_momenta(p, gauge_force(dims, U, beta, c), lam * dt)
+    for i in range(nsteps):
+        U = md_update_links(U, p, dt / 2)
+        p = md_update_momenta(p, gauge_force(dims, U, beta, c), (1 - 2 * lam) * dt)
+        U = md_update_links(U, p, dt / 2)
+        p = md_update_momenta(p, gauge_force(dims, U, beta, c),
+                              2 * lam * dt if i < nsteps - 1 else lam * dt)
+    return U, p
+
+
 def hamiltonian(dims, U, p, beta: float, c) -> float:
     return kinetic_energy(p) + gauge_action(dims, U, beta, c)

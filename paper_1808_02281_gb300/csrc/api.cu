@@ -357,6 +357,50 @@ int lqcd_md_update_links(const lqcd_desc *desc, void *links, const void *mom, do
     return cuda_status(lqcd::launch_update_links(a, as_stream(stream)));
 }
 
+int lqcd_omega_gradient(const lqcd_desc *desc, const void *omega, const void *force, void *grad,
+                        void *stream)
+{
+    int s = check_desc(desc);
+    if (s) return s;
+    if ((s = check_ptrs({omega, force, grad}))) return s;
+    if (grad == omega || grad == force) return LQCD_ERR_ARG;
+    lqcd::MdArgs a{};
+    copy_dims(a.dims, desc);
+    a.precision = desc->precision;
+    a.mom = omega;
+    a.force = force;
+    a.mom_out = grad;
+    return cuda_status(lqcd::launch_omega_gradient(a, as_stream(stream)));
+}
+
+static int convert_common(const lqcd_desc *desc, const void *src, int dst_precision, void *dst,
+                          bool links, void *stream)
+{
+    int s = check_desc(desc);
+    if (s) return s;
+    if ((s = check_ptrs({src, dst}))) return s;
+    if (dst_precision != LQCD_F32 && dst_precision != LQCD_F64) return LQCD_ERR_ARG;
+    if (src == dst) return LQCD_ERR_ARG;
+    lqcd::MdArgs a{};
+    copy_dims(a.dims, desc);
+    a.precision = desc->precision;
+    a.full_in = src;
+    a.full_out = dst;
+    return cuda_status(lqcd::launch_convert(a, dst_precision, links, as_stream(stream)));
+}
+
+int lqcd_convert_links(const lqcd_desc *desc, const void *src, int dst_precision, void *dst,
+                       void *stream)
+{
+    return convert_common(desc, src, dst_precision, dst, true, stream);
+}
+
+int lqcd_convert_algebra(const lqcd_desc *desc, const void *src, int dst_precision, void *dst,
+                         void *stream)
+{
+    return convert_common(desc, src, dst_precision, dst, false, stream);
+}
+
 int lqcd_pack_links(const lqcd_desc *desc, const void *full, void *links, void *stream)
 {
     int s = check_desc(desc);

@@ -111,6 +111,9 @@ struct MdArgs {
 cudaError_t launch_update_momenta(const MdArgs &a, cudaStream_t st);
 cudaError_t launch_update_links(const MdArgs &a, cudaStream_t st);
 cudaError_t launch_links_from_omega(const MdArgs &a, cudaStream_t st);
+cudaError_t launch_omega_gradient(const MdArgs &a, cudaStream_t st);
+// full_in -> full_out in another precision; links: 12 reals per item, else 8
+cudaError_t launch_convert(const MdArgs &a, int dst_precision, bool links, cudaStream_t st);
 cudaError_t launch_pack(const MdArgs &a, cudaStream_t st);
 cudaError_t launch_unpack(const MdArgs &a, cudaStream_t st);
 

@@ -92,6 +92,100 @@ __global__ void __launch_bounds__(kBlock) update_links(R *__restrict__ links,
     }
 }
 
+// Chain rule through U = exp(X) U0, X = i W, W = omega.T (Eq. 18_1_29_3).
+// A change d omega moves U by the left perturbation exp(i delta.T) with
+// i delta.T = phi(ad_X)(i d omega.T), phi(z) = (e^z - 1)/z.  The force gives
+// the left derivative dS/d delta^b = -f^b, so
+//     dS/d omega^a = components of phi(-ad_X)(-i F),   F = f.T,
+// since phi(ad_X) is orthogonal-adjoint to phi(-ad_X) on su(3).  Writing the
+// series terms as -i H_n with Hermitian H_n:
+//     H_0 = F,   H_n = -i [W, H_{n-1}] / (n+1),   A = sum_n H_n,
+//     dS/d omega^a = -tr(lambda_a A)  (= -f^a at omega = 0).
+// The series stops once (2 |W|_F)^n / (n+1)!, a bound on |H_n|/|F|, is below
+// the working precision.
+template <typename R>
+__global__ void __launch_bounds__(kBlock) omega_gradient(const R *__restrict__ omega,
+                                                         const R *__restrict__ force,
+                                                         R *__restrict__ grad, int64_t V)
+{
+    constexpr int NMAX = sizeof(R) == 8 ? 40 : 24;
+    const R eps = sizeof(R) == 8 ? R(1e-17) : R(1e-9);
+    const int64_t nlinks = 4 * V;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nlinks;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int mu = (int)(i / V);
+        const int64_t n = i - mu * V;
+        R w[8], f[8];
+        load_algebra(omega, V, mu, n, w);
+        load_algebra(force, V, mu, n, f);
+        const Mat<R> W = algebra_matrix(w);
+        Mat<R> h = algebra_matrix(f); // H_0 = F
+        Mat<R> acc = h;
+        R wn = R(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) wn += W.re[a][b] * W.re[a][b] + W.im[a][b] * W.im[a][b];
+        const R bound = R(2) * sqrt(wn);
+        R est = R(1);
+        for (int k = 1; k <= NMAX; ++k) {
+            const Mat<R> wh = mul<N, N>(W, h);
+            const Mat<R> hw = mul<N, N>(h, W);
+            const R inv = R(1) / R(k + 1);
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    // H_k = -i (cr + i ci) / (k+1) with [W, H_{k-1}] = cr + i ci
+                    const R cr = wh.re[a][b] - hw.re[a][b], ci = wh.im[a][b] - hw.im[a][b];
+                    h.re[a][b] = ci * inv;
+                    h.im[a][b] = -cr * inv;
+                    acc.re[a][b] += h.re[a][b];
+                    acc.im[a][b] += h.im[a][b];
+                }
+            est *= bound * inv;
+            if (est < eps) break;
+        }
+        // dS/d omega^a = -tr(lambda_a A) (A Hermitian: real traces)
+        R g[8];
+        g[0] = -(acc.re[0][1] + acc.re[1][0]);
+        g[1] = -(acc.im[1][0] - acc.im[0][1]);
+        g[2] = -(acc.re[0][0] - acc.re[1][1]);
+        g[3] = -(acc.re[0][2] + acc.re[2][0]);
+        g[4] = -(acc.im[2][0] - acc.im[0][2]);
+        g[5] = -(acc.re[1][2] + acc.re[2][1]);
+        g[6] = -(acc.im[2][1] - acc.im[1][2]);
+        g[7] = -R(0.57735026918962576451) * (acc.re[0][0] + acc.re[1][1] - R(2) * acc.re[2][2]);
+        store_algebra(grad, V, mu, n, g);
+    }
+}
+
+// Real r (0..NR-1) of item (n, mu) of a structure-of-arrays field with NR
+// reals per item and W-wide lanes.
+template <typename R, int NR>
+__device__ __forceinline__ int64_t soa_index(int64_t V, int mu, int64_t n, int r)
+{
+    constexpr int W = Vec<R>::W;
+    return (((int64_t)mu * (NR / W) + r / W) * V + n) * W + r % W;
+}
+
+// Precision conversion of a link (NR = 12) or algebra (NR = 8) field; the
+// stored reals are converted one by one (FP32 -> FP64 exactly).
+template <typename RS, typename RD, int NR>
+__global__ void __launch_bounds__(kBlock) convert_field(const RS *__restrict__ src,
+                                                        RD *__restrict__ dst, int64_t V)
+{
+    const int64_t nitems = 4 * V;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nitems;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int mu = (int)(i / V);
+        const int64_t n = i - mu * V;
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+            dst[soa_index<RD, NR>(V, mu, n, r)] = (RD)src[soa_index<RS, NR>(V, mu, n, r)];
+    }
+}
+
 // full [V][4][3][3] (re, im) -> compact link layout (rows 0, 1)
 template <typename R>
 __global__ void __launch_bounds__(kBlock) pack(const R *__restrict__ full, R *__restrict__ links,
@@ -176,6 +270,47 @@ cudaError_t launch_links_from_omega(const MdArgs &a, cudaStream_t st)
         update_links<float, true><<<grid_for(4 * V), kBlock, 0, st>>>(
             static_cast<float *>(a.links), static_cast<const float *>(a.mom), V, 1.0f);
     return cudaGetLastError();
+}
+
+cudaError_t launch_omega_gradient(const MdArgs &a, cudaStream_t st)
+{
+    const int64_t V = volume(a.dims);
+    if (a.precision == LQCD_F64)
+        omega_gradient<double><<<grid_for(4 * V), kBlock, 0, st>>>(
+            static_cast<const double *>(a.mom), static_cast<const double *>(a.force),
+            static_cast<double *>(a.mom_out), V);
+    else
+        omega_gradient<float><<<grid_for(4 * V), kBlock, 0, st>>>(
+            static_cast<const float *>(a.mom), static_cast<const float *>(a.force),
+            static_cast<float *>(a.mom_out), V);
+    return cudaGetLastError();
+}
+
+template <int NR> static cudaError_t launch_convert_t(const MdArgs &a, int dst_precision,
+                                                      cudaStream_t st)
+{
+    const int64_t V = volume(a.dims);
+    const void *src = a.full_in;
+    void *dst = a.full_out;
+    const unsigned grid = grid_for(4 * V);
+    if (a.precision == LQCD_F32 && dst_precision == LQCD_F64)
+        convert_field<float, double, NR><<<grid, kBlock, 0, st>>>(static_cast<const float *>(src),
+                                                                  static_cast<double *>(dst), V);
+    else if (a.precision == LQCD_F64 && dst_precision == LQCD_F32)
+        convert_field<double, float, NR><<<grid, kBlock, 0, st>>>(static_cast<const double *>(src),
+                                                                  static_cast<float *>(dst), V);
+    else if (a.precision == LQCD_F32)
+        convert_field<float, float, NR><<<grid, kBlock, 0, st>>>(static_cast<const float *>(src),
+                                                                 static_cast<float *>(dst), V);
+    else
+        convert_field<double, double, NR><<<grid, kBlock, 0, st>>>(
+            static_cast<const double *>(src), static_cast<double *>(dst), V);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert(const MdArgs &a, int dst_precision, bool links, cudaStream_t st)
+{
+    return links ? launch_convert_t<12>(a, dst_precision, st) : launch_convert_t<8>(a, dst_precision, st);
 }
 
 cudaError_t launch_pack(const MdArgs &a, cudaStream_t st)

@@ -1,0 +1,174 @@
+"""Molecular-dynamics trajectories of the Symanzik gauge action (the HMC use
+of the force, paper Sec. II) on liblqcd's kernels.
+
+Integrators (the paper names none; both are standard symmetric splittings):
+  leapfrog   p(dt/2) [U(dt) p(dt)]^(n-1) U(dt) p(dt/2)            n+1 forces
+  omelyan    2nd-order minimum-norm (Omelyan, Mryglod & Folk, Comput. Phys.
+             Commun. 151 (2003) 272), lambda = 0.1931833275037836:
+             p(l dt) U(dt/2) p((1-2l) dt) U(dt/2) p(l dt) per step,   2n+1 forces
+Every momentum kick is one lqcd_md_force_step (force and p += c f in one
+pass, the force never stored); every drift one lqcd_md_update_links.
+
+The Hamiltonian H = K + S is formed in FP64: K = sum p^2/2 from the stored
+momenta, S from the action kernel, for FP32-stored links either in FP32
+arithmetic or (``action_precision="f64"``) in FP64 arithmetic on the same
+stored values.  A whole trajectory can be captured as one CUDA graph.
+
+``python -m paper_1808_02281_gb300.hmc`` runs the dH-versus-dt study.
+"""
+from __future__ import annotations
+
+import argparse
+import dataclasses
+import json
+import time
+
+import torch
+
+from . import lqcd, synth
+
+OMELYAN_LAMBDA = 0.1931833275037836
+
+
+@dataclasses.dataclass
+class MDState:
+    lat: lqcd.Lattice
+    links: torch.Tensor
+    mom: torch.Tensor
+    workspace: torch.Tensor
+
+    @classmethod
+    def create(cls, lat: lqcd.Lattice, links: torch.Tensor, mom: torch.Tensor) -> "MDState":
+        return cls(lat, links, mom, lqcd.make_workspace(lat, links.device))
+
+    def clone(self) -> "MDState":
+        return MDState(self.lat, self.links.clone(), self.mom.clone(), self.workspace)
+
+
+def kick(st: MDState, coef: float) -> None:
+    """p += coef * f(U)."""
+    lqcd.md_force_step(st.lat, st.links, mom=st.mom, dt=coef, workspace=st.workspace)
+
+
+def drift(st: MDState, coef: float) -> None:
+    """U <- exp(i coef p.T) U."""
+    lqcd.md_update_links(st.lat, st.links, st.mom, coef)
+
+
+def leapfrog(st: MDState, dt: float, nsteps: int) -> None:
+    kick(st, dt / 2)
+    for i in range(nsteps):
+        drift(st, dt)
+        kick(st, dt if i < nsteps - 1 else dt / 2)
+
+
+def omelyan(st: MDState, dt: float, nsteps: int, lam: float = OMELYAN_LAMBDA) -> None:
+    kick(st, lam * dt)
+    for i in range(nsteps):
+        drift(st, dt / 2)
+        kick(st, (1 - 2 * lam) * dt)
+        drift(st, dt / 2)
+        kick(st, 2 * lam * dt if i < nsteps - 1 else lam * dt)
+
+
+INTEGRATORS = {"leapfrog": leapfrog, "omelyan": omelyan}
+
+
+def force_evaluations(integrator: str, nsteps: int) -> int:
+    return nsteps + 1 if integrator == "leapfrog" else 2 * nsteps + 1
+
+
+def hamiltonian(st: MDState, action_precision: str | None = None) -> float:
+    """H = K + S in FP64 (host float; synchronises)."""
+    lat = st.lat
+    K = lqcd.kinetic_energy(lat, st.mom, workspace=st.workspace)
+    prec = action_precision or lat.precision
+    if prec == lat.precision:
+        S = lqcd.gauge_action(lat, st.links, workspace=st.workspace)
+    else:
+        lat2 = lat.with_(precision=prec)
+        S = lqcd.gauge_action(lat2, lqcd.convert_links(lat, st.links, prec))
+    return float(K.item()) + float(S.item())
+
+
+def trajectory(st: MDState, tau: float, dt: float, integrator: str = "omelyan",
+               action_precision: str | None = None) -> float:
+    """Integrate one trajectory of length tau in place; return dH."""
+    nsteps = max(1, int(round(tau / dt)))
+    H0 = hamiltonian(st, action_precision)
+    INTEGRATORS[integrator](st, tau / nsteps, nsteps)
+    return hamiltonian(st, action_precision) - H0
+
+
+class GraphTrajectory:
+    """One trajectory (fixed dt and number of steps) captured as a CUDA graph
+    on the tensors of ``st``; replay() integrates them in place."""
+
+    def __init__(self, st: MDState, dt: float, nsteps: int, integrator: str = "omelyan"):
+        self.st = st
+        run = INTEGRATORS[integrator]
+        # first launches (one-time device set-up of the library) outside capture
+        scratch = st.clone()
+        run(scratch, dt, 1)
+        torch.cuda.synchronize()
+        del scratch
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            run(st, dt, nsteps)
+
+    def replay(self) -> None:
+        self.graph.replay()
+
+
+def initial_state(dims, precision: str, sigma: float = 0.3, u0: float = 0.87,
+                  beta: float = 6.0, seed: int = 0, device="cuda") -> MDState:
+    """Links exp(i w.T), w ~ N(0, sigma^2) and Gaussian momenta, both from the
+    seeded generator (the same draws for either precision)."""
+    lat = lqcd.Lattice.symanzik(dims, beta, u0, precision)
+    links = lqcd.links_from_omega(lat, lqcd.algebra_to_device(lat, synth.omega(dims, sigma, seed), device))
+    mom = lqcd.algebra_to_device(lat, synth.momenta(dims, seed + 1), device)
+    return MDState.create(lat, links, mom)
+
+
+def dh_study(dims, tau: float, dts, integrator: str, precisions, seed: int = 0):
+    """dH against dt for each precision; FP32 runs also report dH with the
+    FP64 action of their stored links.  Yields one dict per (precision, dt)."""
+    for prec in precisions:
+        for dt in dts:
+            st = initial_state(dims, prec, seed=seed)
+            nsteps = max(1, int(round(tau / dt)))
+            H0 = hamiltonian(st)
+            H0_64 = hamiltonian(st, "f64") if prec == "f32" else H0
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            INTEGRATORS[integrator](st, tau / nsteps, nsteps)
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t0
+            rec = {"precision": prec, "dims": list(dims), "tau": tau, "dt": tau / nsteps,
+                   "nsteps": nsteps, "integrator": integrator, "dH": hamiltonian(st) - H0,
+                   "seconds": secs, "forces": force_evaluations(integrator, nsteps)}
+            if prec == "f32":
+                rec["dH_f64_action"] = hamiltonian(st, "f64") - H0_64
+            yield rec
+            del st
+            torch.cuda.empty_cache()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description="dH against dt for FP32 and FP64 trajectories")
+    ap.add_argument("--dims", type=int, nargs=4, default=[48, 48, 48, 96])
+    ap.add_argument("--tau", type=float, default=1.0)
+    ap.add_argument("--dts", type=float, nargs="+", default=[0.05, 0.025, 0.0125])
+    ap.add_argument("--integrator", choices=sorted(INTEGRATORS), default="omelyan")
+    ap.add_argument("--precisions", nargs="+", default=["f32", "f64"])
+    ap.add_argument("--seed", type=int, default=0)
+    args = ap.parse_args(argv)
+    from . import build
+    build.build()
+    for rec in dh_study(tuple(args.dims), args.tau, args.dts, args.integrator, args.precisions,
+                        args.seed):
+        print(json.dumps(rec), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -64,6 +64,12 @@ _EXPORTS = {
                                               ctypes.c_double, ctypes.c_void_p]),
     "lqcd_md_update_links": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_double, ctypes.c_void_p]),
+    "lqcd_omega_gradient": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p]),
+    "lqcd_convert_links": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_void_p]),
+    "lqcd_convert_algebra": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                            ctypes.c_void_p]),
     "lqcd_pack_links": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "lqcd_unpack_links": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "lqcd_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(Desc)]),
@@ -309,6 +315,41 @@ def md_update_links(lat: Lattice, links: torch.Tensor, mom: torch.Tensor, dt: fl
     _call("lqcd_md_update_links", ctypes.byref(d), _ptr(links), _ptr(mom), float(dt),
           _stream(stream))
     return links
+
+
+def omega_gradient(lat: Lattice, omega: torch.Tensor, force: torch.Tensor,
+                   out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """dS/domega for U = exp(i omega.T) U0, from the force at U."""
+    _check(omega, lat, lat.algebra_shape, "omega")
+    _check(force, lat, lat.algebra_shape, "force")
+    out = empty_algebra(lat, omega.device) if out is None else out
+    _check(out, lat, lat.algebra_shape, "grad")
+    d = lat.desc()
+    _call("lqcd_omega_gradient", ctypes.byref(d), _ptr(omega), _ptr(force), _ptr(out),
+          _stream(stream))
+    return out
+
+
+def convert_links(lat: Lattice, links: torch.Tensor, precision: str, stream=None) -> torch.Tensor:
+    """The same links stored in another precision (new tensor)."""
+    _check(links, lat, lat.link_shape, "links")
+    dst_lat = lat.with_(precision=precision)
+    out = empty_links(dst_lat, links.device)
+    d = lat.desc()
+    _call("lqcd_convert_links", ctypes.byref(d), _ptr(links), F32 if precision == "f32" else F64,
+          _ptr(out), _stream(stream))
+    return out
+
+
+def convert_algebra(lat: Lattice, field: torch.Tensor, precision: str, stream=None) -> torch.Tensor:
+    """The same algebra field (momenta, force) in another precision."""
+    _check(field, lat, lat.algebra_shape, "field")
+    dst_lat = lat.with_(precision=precision)
+    out = empty_algebra(dst_lat, field.device)
+    d = lat.desc()
+    _call("lqcd_convert_algebra", ctypes.byref(d), _ptr(field), F32 if precision == "f32" else F64,
+          _ptr(out), _stream(stream))
+    return out
 
 
 def pack_links(lat: Lattice, full: torch.Tensor, out: torch.Tensor | None = None,

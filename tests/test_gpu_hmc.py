@@ -1,0 +1,109 @@
+"""MD trajectories on the GPU (leapfrog, Omelyan; FP32 and FP64; eager and
+CUDA-graph) against the oracle's integrators and the integrators' own
+invariants."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_1808_02281_gb300 import build as B
+from paper_1808_02281_gb300 import hmc, lqcd, synth
+
+pytestmark = pytest.mark.gpu
+
+DIMS = (4, 4, 4, 4)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.build()
+
+
+def _state(prec, sigma=0.5, seed=0):
+    return hmc.initial_state(DIMS, prec, sigma=sigma, u0=0.87, seed=seed)
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-11), ("f32", 5e-5)])
+@pytest.mark.parametrize("integrator", ["leapfrog", "omelyan"])
+def test_trajectory_matches_oracle(prec, tol, integrator):
+    st = _state(prec)
+    w = synth.omega(DIMS, 0.5, 0)
+    p = synth.momenta(DIMS, 1)
+    U_ref, p_ref = O.links_from_omega(w), p
+    c = O.coefficients(0.87)
+    dt, n = 0.05, 3
+    getattr(hmc, integrator)(st, dt, n)
+    U_ref, p_ref = getattr(O, integrator)(DIMS, U_ref, p_ref, 6.0, c, dt, n)
+    U = lqcd.full_from_device(lqcd.unpack_links(st.lat, st.links))
+    pg = lqcd.algebra_from_device(st.mom)
+    assert np.abs(U - U_ref).max() < tol
+    assert np.abs(pg - p_ref).max() < tol * max(1.0, np.abs(p_ref).max())
+
+
+@pytest.mark.parametrize("integrator", ["leapfrog", "omelyan"])
+def test_reversibility_fp64(integrator):
+    st = _state("f64")
+    U0, p0 = st.links.clone(), st.mom.clone()
+    run = hmc.INTEGRATORS[integrator]
+    run(st, 0.05, 6)
+    st.mom.neg_()
+    run(st, 0.05, 6)
+    st.mom.neg_()
+    assert float((st.links - U0).abs().max()) < 1e-11
+    assert float((st.mom - p0).abs().max()) < 1e-10
+
+
+@pytest.mark.parametrize("integrator", ["leapfrog", "omelyan"])
+def test_energy_violation_second_order(integrator):
+    """dH ~ dt^2 (ratio 4 when dt halves) in FP64; matches the oracle's dH."""
+    tau = 0.4
+    dH = []
+    for n in (4, 8):
+        st = _state("f64")
+        dH.append(hmc.trajectory(st, tau, tau / n, integrator))
+    assert 3.0 < dH[0] / dH[1] < 5.0, dH
+    w = synth.omega(DIMS, 0.5, 0)
+    p = synth.momenta(DIMS, 1)
+    U = O.links_from_omega(w)
+    c = O.coefficients(0.87)
+    U1, p1 = getattr(O, integrator)(DIMS, U, p, 6.0, c, tau / 8, 8)
+    dH_ref = O.hamiltonian(DIMS, U1, p1, 6.0, c) - O.hamiltonian(DIMS, U, p, 6.0, c)
+    assert abs(dH[1] - dH_ref) < 1e-9 * max(1.0, abs(O.hamiltonian(DIMS, U, p, 6.0, c)))
+
+
+def test_fp32_dh_close_to_fp64():
+    """The FP32 trajectory's dH, with the action of its FP32-stored links
+    evaluated in FP64, tracks the FP64 trajectory's dH."""
+    dims = (8, 8, 8, 8)
+    out = {}
+    for prec in ("f32", "f64"):
+        st = hmc.initial_state(dims, prec, sigma=0.3, seed=2)
+        out[prec] = hmc.trajectory(st, 0.5, 0.05, "omelyan", action_precision="f64")
+    assert abs(out["f32"] - out["f64"]) < 2e-2 * max(1.0, abs(out["f64"])), out
+
+
+def test_cuda_graph_replay_equals_eager():
+    st = _state("f32", seed=4)
+    eager = st.clone()
+    hmc.omelyan(eager, 0.05, 5)
+    g = hmc.GraphTrajectory(st, 0.05, 5, "omelyan")
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(st.links, eager.links)
+    assert torch.equal(st.mom, eager.mom)
+
+
+def test_convert_roundtrip():
+    lat = lqcd.Lattice.symanzik(DIMS, 6.0, 0.87, "f32")
+    U = lqcd.links_from_omega(lat, lqcd.algebra_to_device(lat, synth.omega(DIMS, 0.5, 0)))
+    U64 = lqcd.convert_links(lat, U, "f64")
+    back = lqcd.convert_links(lat.with_(precision="f64"), U64, "f32")
+    assert torch.equal(back, U)
+    full32 = lqcd.unpack_links(lat, U).double()
+    full64 = lqcd.unpack_links(lat.with_(precision="f64"), U64)
+    assert float((full64[..., :2, :, :] - full32[..., :2, :, :]).abs().max()) == 0.0
+    p = lqcd.algebra_to_device(lat, synth.momenta(DIMS, 3))
+    p64 = lqcd.convert_algebra(lat, p, "f64")
+    np.testing.assert_array_equal(lqcd.algebra_from_device(p64), lqcd.algebra_from_device(p))

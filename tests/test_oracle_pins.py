@@ -378,3 +378,25 @@ def test_leapfrog_reversible_and_second_order(c1):
             assert np.abs(-p0 - p).max() < 1e-10
     ratio = dH[0] / dH[1]
     assert 3.0 < ratio < 5.0, (dH, ratio)
+
+
+def test_omelyan_reversible_and_second_order(c1):
+    """The oracle's Omelyan integrator: reversible to roundoff, dH ~ dt^2, and
+    smaller |dH| than leapfrog at the same step size."""
+    U, c = c1
+    p = synth.momenta(DIMS4, seed=5)
+    tau = 0.2
+    dH = []
+    for nsteps in (2, 4):
+        dt = tau / nsteps
+        U1, p1 = O.omelyan(DIMS4, U, p, BETA, c, dt, nsteps)
+        dH.append(O.hamiltonian(DIMS4, U1, p1, BETA, c) - O.hamiltonian(DIMS4, U, p, BETA, c))
+        if nsteps == 2:
+            U0, p0 = O.omelyan(DIMS4, U1, -p1, BETA, c, dt, nsteps)
+            assert np.abs(U0 - U).max() < 1e-11
+            assert np.abs(-p0 - p).max() < 1e-10
+            Ul, pl = O.leapfrog(DIMS4, U, p, BETA, c, dt, nsteps)
+            dH_lf = O.hamiltonian(DIMS4, Ul, pl, BETA, c) - O.hamiltonian(DIMS4, U, p, BETA, c)
+            assert abs(dH[0]) < abs(dH_lf)
+    ratio = dH[0] / dH[1]
+    assert 3.0 < ratio < 5.0, (dH, ratio)
