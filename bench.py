@@ -361,6 +361,49 @@ def run_ours(args):
     del st, g_traj
     torch.cuda.empty_cache()
 
+    # uneven-volume batch: 4 each of 8^4, 12^3x24, 16^3x32, 24^3x48 (FP32)
+    bs = hmc.initial_batch(synth.BATCH_DIMS, "f32", w["sigma"], w["u0"], w["beta"], w["seed"] + rank)
+    nl_batch = sum(4 * synth.volume(d) for d in bs.dims)
+    actions = torch.empty(len(bs.dims), dtype=torch.float64, device=dev)
+
+    def batch_step():
+        lqcd.md_force_step_batched(bs.params, bs.dims, bs.links, mom=bs.mom, dt=DT,
+                                   actions=actions, workspace=bs.workspace)
+        lqcd.md_update_links_batched(bs.params, bs.dims, bs.links, bs.mom, DT)
+
+    def single_steps():
+        for c, d in enumerate(bs.dims):
+            lat_c = bs.params.with_(dims=d)
+            lqcd.md_force_step(lat_c, bs.links[c], mom=bs.mom[c], dt=DT, action=actions[c],
+                               workspace=bs.workspace)
+            lqcd.md_update_links(lat_c, bs.links[c], bs.mom[c], DT)
+
+    def time_it(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_.record(stream)
+        for _ in range(reps):
+            fn()
+        b_.record(stream)
+        torch.cuda.synchronize(dev)
+        return a_.elapsed_time(b_) / reps
+
+    ms_batched = time_it(batch_step, 10)
+    ms_single = time_it(single_steps, 10)
+    g_batch = hmc.GraphBatchTrajectory(bs, DT, 20, "leapfrog")
+    ms_graph = time_it(g_batch.replay, 3)
+    ms_eager = time_it(lambda: hmc.batch_leapfrog(bs, DT, 20), 3)
+    batch = {"lattices": len(bs.dims), "links": nl_batch,
+             "step_ms_batched": ms_batched, "step_ms_per_lattice_calls": ms_single,
+             "glinks_batched": nl_batch / (ms_batched / 1e3) / 1e9,
+             "glinks_per_lattice_calls": nl_batch / (ms_single / 1e3) / 1e9,
+             "trajectory": "leapfrog, 20 steps, dt 0.05",
+             "trajectory_graph_ms": ms_graph, "trajectory_eager_ms": ms_eager}
+    del bs, g_batch, actions
+    torch.cuda.empty_cache()
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -415,6 +458,7 @@ def run_ours(args):
                 "force_glinks": nlinks / (per64["force"] / 1e3) / 1e9, "steps": k64},
         "action_f32": S32, "action_f64": S64,
         "dH": dh,
+        "batch": batch,
         "roofline": roofline,
         "streaming": streaming,
         "cpu_baseline": cpu,

@@ -161,6 +161,38 @@ LQCD_API int lqcd_set_force_variant(const lqcd_desc *desc, int variant);
 LQCD_API int lqcd_autotune_force(const lqcd_desc *desc, const void *links, void *force, void *workspace,
                         size_t workspace_bytes, int reps, void *stream, int *best, float *ms);
 
+/* Batches: up to LQCD_MAX_BATCH lattices of any extents (and the same
+ * precision and action parameters, taken from the descriptor; desc->dims is
+ * ignored) in ONE persistent launch per pass.  Each entry names its lattice:
+ *   dims   extents of this lattice;
+ *   links  link layout (force step: read; link step: read and written);
+ *   mom    algebra layout (force step: p += dt f if set; link step: read);
+ *   force  algebra layout, f written if set (force step);
+ *   action one device double, S_G written if set (force step).
+ * lqcd_md_force_step_batched uses the staple-field algorithm (force_algo
+ * AUTO or STAPLE_FIELDS, else LQCD_ERR_UNSUPPORTED) with a workspace of
+ * lqcd_workspace_bytes_batched bytes (the single-lattice workspaces back to
+ * back); every lattice gets exactly the result of its own
+ * lqcd_md_force_step, bit for bit.  lqcd_md_update_links_batched is the link
+ * step U <- exp(i dt p.T) U of every lattice. */
+#define LQCD_MAX_BATCH 64
+typedef struct lqcd_lattice_ref {
+    int32_t dims[4];
+    int32_t reserved[4];
+    const void *links;
+    void *mom;
+    void *force;
+    double *action;
+} lqcd_lattice_ref;
+
+LQCD_API size_t lqcd_workspace_bytes_batched(const lqcd_desc *desc, int n,
+                                             const lqcd_lattice_ref *lats);
+LQCD_API int lqcd_md_force_step_batched(const lqcd_desc *desc, int n, const lqcd_lattice_ref *lats,
+                                        double dt, void *workspace, size_t workspace_bytes,
+                                        void *stream);
+LQCD_API int lqcd_md_update_links_batched(const lqcd_desc *desc, int n,
+                                          const lqcd_lattice_ref *lats, double dt, void *stream);
+
 /* Gauge action S_G = (beta/3) sum_n sum_{34 loops P} c_P [3 - Re tr P_n]
  * (Eq. 18_6_4_1).  links: link layout (device, read).  action: ONE double in
  * device memory (written, FP64 in both precisions: per-loop terms and all

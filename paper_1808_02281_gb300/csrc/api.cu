@@ -200,6 +200,106 @@ int lqcd_md_force_step(const lqcd_desc *desc, const void *links, void *force, vo
     return run_force(desc, links, force, mom, dt, action, workspace, workspace_bytes, stream);
 }
 
+namespace {
+
+// Batched calls: the descriptor supplies precision, coefficients and the
+// algorithm; every entry its own extents.
+int check_batch(const lqcd_desc *desc, int n, const lqcd_lattice_ref *lats)
+{
+    int s = check_desc(desc);
+    if (s) return s;
+    if (n < 1 || n > LQCD_MAX_BATCH || lats == nullptr) return LQCD_ERR_ARG;
+    for (int c = 0; c < n; ++c) {
+        lqcd_desc d = *desc;
+        for (int i = 0; i < 4; ++i) d.dims[i] = lats[c].dims[i];
+        if ((s = check_desc(&d))) return s;
+        if ((s = check_ptrs({lats[c].links}))) return s;
+        if (lats[c].mom != nullptr && !aligned16(lats[c].mom)) return LQCD_ERR_ALIGN;
+        if (lats[c].force != nullptr && !aligned16(lats[c].force)) return LQCD_ERR_ALIGN;
+        if (lats[c].action != nullptr && ((uintptr_t)lats[c].action & 7u) != 0) return LQCD_ERR_ALIGN;
+    }
+    return LQCD_OK;
+}
+
+size_t batch_workspace_bytes(const lqcd_desc *desc, int n, const lqcd_lattice_ref *lats)
+{
+    size_t total = 0;
+    for (int c = 0; c < n; ++c) {
+        lqcd_desc d = *desc;
+        for (int i = 0; i < 4; ++i) d.dims[i] = lats[c].dims[i];
+        total += staple_workspace_bytes(&d);
+    }
+    return total + lqcd::kBatchCounterBytes;
+}
+
+} // namespace
+
+size_t lqcd_workspace_bytes_batched(const lqcd_desc *desc, int n, const lqcd_lattice_ref *lats)
+{
+    if (check_batch(desc, n, lats) != LQCD_OK) return 0;
+    return batch_workspace_bytes(desc, n, lats);
+}
+
+int lqcd_md_force_step_batched(const lqcd_desc *desc, int n, const lqcd_lattice_ref *lats,
+                               double dt, void *workspace, size_t workspace_bytes, void *stream)
+{
+    int s = check_batch(desc, n, lats);
+    if (s) return s;
+    if (desc->force_algo != LQCD_FORCE_AUTO && desc->force_algo != LQCD_FORCE_STAPLE_FIELDS)
+        return LQCD_ERR_UNSUPPORTED;
+    if (!std::isfinite(dt)) return LQCD_ERR_ARG;
+    for (int c = 0; c < n; ++c)
+        if (lats[c].force == nullptr && lats[c].mom == nullptr && lats[c].action == nullptr)
+            return LQCD_ERR_ARG;
+    if (!workspace_fits(workspace, workspace_bytes, batch_workspace_bytes(desc, n, lats)))
+        return LQCD_ERR_WORKSPACE;
+    lqcd::SfLattice items[LQCD_MAX_BATCH];
+    char *ws = static_cast<char *>(workspace);
+    for (int c = 0; c < n; ++c) {
+        lqcd::SfLattice &L = items[c];
+        L = lqcd::SfLattice{};
+        for (int i = 0; i < 4; ++i) L.dims[i] = lats[c].dims[i];
+        L.links = lats[c].links;
+        L.force = lats[c].force;
+        L.mom = lats[c].mom;
+        L.action = lats[c].action;
+        const size_t sf = lqcd::staple_field_bytes(L.dims, desc->precision);
+        L.staples = ws;
+        L.partials = reinterpret_cast<double *>(ws + sf);
+        lqcd_desc d = *desc;
+        for (int i = 0; i < 4; ++i) d.dims[i] = lats[c].dims[i];
+        ws += staple_workspace_bytes(&d);
+    }
+    lqcd::ForceArgs a{};
+    a.precision = desc->precision;
+    a.beta = desc->beta;
+    a.c_plaq = desc->c_plaq;
+    a.c_rect = desc->c_rect;
+    a.c_cube = desc->c_cube;
+    a.dt = dt;
+    a.variant = -1;
+    auto *counter = reinterpret_cast<unsigned long long *>(ws); // after the last lattice's part
+    return cuda_status(
+        lqcd::launch_force_staple_fields_batched(a, n, items, counter, as_stream(stream)));
+}
+
+int lqcd_md_update_links_batched(const lqcd_desc *desc, int n, const lqcd_lattice_ref *lats,
+                                 double dt, void *stream)
+{
+    int s = check_batch(desc, n, lats);
+    if (s) return s;
+    if (!std::isfinite(dt)) return LQCD_ERR_ARG;
+    lqcd::LinkStepItem items[LQCD_MAX_BATCH];
+    for (int c = 0; c < n; ++c) {
+        if (lats[c].mom == nullptr || lats[c].mom == lats[c].links) return LQCD_ERR_ARG;
+        items[c].V = (int64_t)lats[c].dims[0] * lats[c].dims[1] * lats[c].dims[2] * lats[c].dims[3];
+        items[c].links = const_cast<void *>(lats[c].links);
+        items[c].mom = lats[c].mom;
+    }
+    return cuda_status(
+        lqcd::launch_update_links_batched(desc->precision, n, items, dt, as_stream(stream)));
+}
+
 int lqcd_force_variant_count(const lqcd_desc *desc)
 {
     const int s = check_desc(desc);

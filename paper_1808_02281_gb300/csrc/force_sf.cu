@@ -29,7 +29,19 @@
 // (L = 4 or 6 times) with its c_P, so with the plaquette staple sum Pl,
 //   S_G = (beta/3) sum_links [ 3 (1.5 c_plaq + 3 c_rect + 4 c_cube)
 //                              - Re tr(U t)/6 - (c_plaq/12) Re tr(U Pl) ]
-// (Eq. 18_6_4_1), each link's term formed in FP64 from its two traces.
+// (Eq. 18_6_4_1), each link's share formed in the working precision from its
+// two traces and summed in FP64.
+//
+// Work decomposition.  Both passes run in "virtual blocks" of 128 threads:
+// the four warps of a block take the four directions of the same 32 sites
+// (the planes around a site are read while they are in L1/L2, and each warp
+// reads one plane per instruction, so a quarter-warp covers 8 consecutive
+// sites of one 128-byte line).  A single lattice is launched with one CTA per
+// virtual block; a batch of lattices of different extents runs as one
+// persistent launch whose CTAs take the virtual blocks of all lattices from
+// a work counter.  The
+// action partial sum of a virtual block is the same in both, so a batched
+// result equals the single-lattice result bit for bit.
 #include <atomic>
 #include <mutex>
 
@@ -40,75 +52,40 @@ namespace lqcd {
 
 namespace {
 
-constexpr int kBlockA = 128; // four warps: the four directions of 32 sites
-constexpr int kBlockB = 128; // four warps: the four directions of 32 sites
+constexpr int kBlock = 128; // four warps: the four directions of 32 sites
 
 __host__ __device__ __forceinline__ int64_t padded_sites(int64_t V) { return (V + 31) & ~(int64_t)31; }
-
-// ---------------------------------------------------------------- pass A
-
-template <typename R>
-__global__ void __launch_bounds__(kBlockA) staple_fields(const R *__restrict__ links,
-                                                         R *__restrict__ sf, Geom g)
-{
-    // four warps per block: the four directions of 32 consecutive sites, so
-    // the links around a site are read once from DRAM (a direction-major
-    // order re-reads the neighbouring directions once per direction)
-    const int64_t nthreads = 4 * padded_sites(g.V);
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nthreads;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int mu = (int)((i >> 5) & 3);
-        const int64_t x = ((i >> 7) << 5) | (i & 31);
-        if (x >= g.V) continue;
-        const Coord c = coord_of(g, x);
-        const int64_t xm = x + disp(g, c, mu, 1); // x + mu
-#pragma unroll 1
-        for (int iv = 0; iv < 3; ++iv) {
-            const int nu = (mu + 1 + iv) & 3;
-            const int64_t vp = disp(g, c, nu, 1), vm = disp(g, c, nu, -1);
-            // b = +nu:  U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
-            Mat<R> t = mul<N, D>(load_link(links, g.V, nu, xm), load_link(links, g.V, mu, x + vp));
-            store_link(sf, g.V, mu * 6 + 2 * iv, x, mul_top2<N, D>(t, load_link(links, g.V, nu, x)));
-            // b = -nu:  U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu)
-            t = mul<D, D>(load_link(links, g.V, nu, xm + vm), load_link(links, g.V, mu, x + vm));
-            store_link(sf, g.V, mu * 6 + 2 * iv + 1, x,
-                       mul_top2<N, N>(t, load_link(links, g.V, nu, x + vm)));
-        }
-    }
-}
-
-// ---------------------------------------------------------------- pass B
+__host__ __device__ __forceinline__ int64_t virtual_blocks(int64_t V) { return padded_sites(V) / 32; }
 
 enum { SC_BETA6 = 0, SC_CPL, SC_CRT, SC_CCB, SC_ACT, SC_ACTPL, SC_DT };
 
-template <typename R> __device__ __forceinline__ R scalar(const ForceArgs &a, int i)
+template <typename R> __device__ __forceinline__ R scalar(const KernelScalars &s, int i)
 {
-    if constexpr (sizeof(R) == 4) return a.sc.f[i];
-    else return a.sc.d[i];
+    if constexpr (sizeof(R) == 4) return s.f[i];
+    else return s.d[i];
 }
 
 // Traversal order of pass B: the lattice is cut into spatial blocks of
 // bx x by x bz sites that run over all t; blocks one after the other, inside
 // a block t-slice by t-slice, inside a slice micro-tiles of mx x my x mz
-// sites (x fastest within and between micro-tiles), and the four links of a
-// site next to each other.  The staple planes of three neighbouring t-slices
-// of one block then stay in L2 while the block is swept, and a micro-tile
-// makes the y and z neighbours of most sites in a thread block L1 hits.
+// sites (x fastest within and between micro-tiles).  The staple planes of
+// three neighbouring t-slices of one block then stay in L2 while the block
+// is swept, and micro-tiles make y and z neighbours L1 hits.
 struct Sweep {
     int bx, by, bz, mx, my, mz;
     int nbx, nby, nmx, nmy, mvol;
     int64_t slice, vol; // sites per block slice and per block
 };
 
-__device__ __forceinline__ Sweep make_sweep(const ForceArgs &a, const Geom &g)
+__device__ __forceinline__ Sweep make_sweep(const SfLattice &L, const Geom &g)
 {
     Sweep s;
-    s.bx = a.sweep[0];
-    s.by = a.sweep[1];
-    s.bz = a.sweep[2];
-    s.mx = a.micro[0];
-    s.my = a.micro[1];
-    s.mz = a.micro[2];
+    s.bx = L.sweep[0];
+    s.by = L.sweep[1];
+    s.bz = L.sweep[2];
+    s.mx = L.micro[0];
+    s.my = L.micro[1];
+    s.mz = L.micro[2];
     s.nbx = g.L0 / s.bx;
     s.nby = g.L1 / s.by;
     s.nmx = s.bx / s.mx;
@@ -139,9 +116,11 @@ __device__ __forceinline__ Coord swept_site(const Sweep &s, int64_t j)
     return c;
 }
 
-__device__ __forceinline__ double block_sum_b(double v)
+// Sum over the block of one double per thread (result in thread 0); the
+// trailing barrier lets the caller run it again in the next virtual block.
+__device__ __forceinline__ double block_sum(double v)
 {
-    __shared__ double part[kBlockB / 32];
+    __shared__ double part[kBlock / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -149,15 +128,88 @@ __device__ __forceinline__ double block_sum_b(double v)
     __syncthreads();
     double s = 0.0;
     if (warp == 0) {
-        s = lane < kBlockB / 32 ? part[lane] : 0.0;
+        s = lane < kBlock / 32 ? part[lane] : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     }
+    __syncthreads();
     return s;
 }
 
+// Next virtual block for a persistent CTA of a batched launch, taken from a
+// work counter: the blocks in flight stay a contiguous window of the sweep
+// (as with hardware block scheduling), which keeps the L2 reuse of the
+// traversal; a fixed stride per CTA would let the window spread out.
+__device__ __forceinline__ int64_t next_virtual_block(unsigned long long *counter)
+{
+    __shared__ unsigned long long s_vb;
+    if (threadIdx.x == 0) s_vb = atomicAdd(counter, 1ull);
+    __syncthreads();
+    const int64_t vb = (int64_t)s_vb;
+    __syncthreads();
+    return vb;
+}
+
+// Lattice of a batch that virtual block vb (global numbering) belongs to.
+__device__ __forceinline__ int batch_entry(const SfBatch &B, int64_t vb)
+{
+    int c = 0;
+    while (c + 1 < B.n && vb >= B.e[c + 1].vb_begin) ++c;
+    return c;
+}
+
+// ---------------------------------------------------------------- pass A
+
+// The 24 staples of the 32 sites of virtual block vb: thread = (site, mu).
+template <typename R>
+__device__ __forceinline__ void staples_block(const SfLattice &L, const Geom &g, int64_t vb)
+{
+    const R *__restrict__ links = static_cast<const R *>(L.links);
+    R *__restrict__ sf = static_cast<R *>(L.staples);
+    const int mu = (int)(threadIdx.x >> 5);
+    const int64_t x = vb * 32 + (threadIdx.x & 31);
+    if (x >= g.V) return;
+    const Coord c = coord_of(g, x);
+    const int64_t xm = x + disp(g, c, mu, 1); // x + mu
+#pragma unroll 1
+    for (int iv = 0; iv < 3; ++iv) {
+        const int nu = (mu + 1 + iv) & 3;
+        const int64_t vp = disp(g, c, nu, 1), vm = disp(g, c, nu, -1);
+        // b = +nu:  U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
+        Mat<R> t = mul<N, D>(load_link(links, g.V, nu, xm), load_link(links, g.V, mu, x + vp));
+        store_link(sf, g.V, mu * 6 + 2 * iv, x, mul_top2<N, D>(t, load_link(links, g.V, nu, x)));
+        // b = -nu:  U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu)
+        t = mul<D, D>(load_link(links, g.V, nu, xm + vm), load_link(links, g.V, mu, x + vm));
+        store_link(sf, g.V, mu * 6 + 2 * iv + 1, x,
+                   mul_top2<N, N>(t, load_link(links, g.V, nu, x + vm)));
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) staple_fields(const __grid_constant__ SfLattice L)
+{
+    const Geom g = make_geom(L.dims);
+    const int64_t nvb = virtual_blocks(g.V);
+    for (int64_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) staples_block<R>(L, g, vb);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) staple_fields_batched(const __grid_constant__ SfBatch B)
+{
+    for (int64_t vb = next_virtual_block(B.counter); vb < B.total;
+         vb = next_virtual_block(B.counter)) {
+        const int c = batch_entry(B, vb);
+        const SfLattice &L = B.e[c];
+        staples_block<R>(L, make_geom(L.dims), vb - L.vb_begin);
+    }
+}
+
+// ---------------------------------------------------------------- pass B
+
 // The staples that start with link(k+rho, d), d = +-nu_d (NEG: minus):
 //   t += B_d [ c_cube sum_{b perp rho, d} S_b(k+d) S^{(d)}_b(k) + c_rect S_d(k+d) A_d^dag ]
+// (the orientation of the shared links fixed at compile time, so that each
+// sign has one small loop body).
 template <bool NEG, bool UNROLLQ, typename R>
 __device__ __forceinline__ void d_terms(Mat<R> &t, const R *__restrict__ links,
                                         const R *__restrict__ sf, const Geom &g, const Coord &c,
@@ -194,366 +246,291 @@ __device__ __forceinline__ void d_terms(Mat<R> &t, const R *__restrict__ links,
     }
 }
 
+// Force (and the fused momentum step) on the 128 links of virtual block vb;
+// returns the thread's share of the action (0 for a padding site).
 template <typename R, bool ACTION, bool UNROLLQ>
-__global__ void __launch_bounds__(kBlockB, sizeof(R) == 4 ? (ACTION ? 3 : 4) : 2)
-    force_from_staples(const ForceArgs a)
+__device__ __forceinline__ double force_block(const SfLattice &L, const KernelScalars &sc,
+                                              const Geom &g, const Sweep &sw, int64_t vb)
 {
-    const Geom g = make_geom(a.dims);
-    const R *__restrict__ links = static_cast<const R *>(a.links);
-    const R *__restrict__ sf = static_cast<const R *>(a.staples);
-    const R c_pl = scalar<R>(a, SC_CPL), c_rt = scalar<R>(a, SC_CRT), c_cb = scalar<R>(a, SC_CCB);
-    const R act_const = scalar<R>(a, SC_ACT), act_cpl = scalar<R>(a, SC_ACTPL);
-    const Sweep sw = make_sweep(a, g);
-    // sites padded to whole warps: thread i takes site ((i >> 7) << 5) | (i & 31)
-    // and direction (i >> 5) & 3; padding sites are skipped
-    const int64_t nthreads = 4 * padded_sites(g.V);
-    double acc = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nthreads;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        if ((((i >> 7) << 5) | (i & 31)) >= g.V) continue;
-        // the four warps of a thread block take the four directions of the
-        // same 32 sites: the staple planes around a site are read while they
-        // are in L1/L2 (a direction-major order re-reads them from DRAM once
-        // per direction), and each warp reads one plane per instruction, so a
-        // quarter-warp covers 8 consecutive sites of one 128-byte line
-        const int rho = (int)((i >> 5) & 3);
-        const Coord c = swept_site(sw, ((i >> 7) << 5) | (i & 31));
-        const int64_t k = index_of(g, c);
-        const int64_t kp = k + disp(g, c, rho, 1), km = k + disp(g, c, rho, -1);
-        const int base = rho * 6;
+    const R *__restrict__ links = static_cast<const R *>(L.links);
+    const R *__restrict__ sf = static_cast<const R *>(L.staples);
+    const int rho = (int)(threadIdx.x >> 5);
+    const int64_t j = vb * 32 + (threadIdx.x & 31);
+    if (j >= g.V) return 0.0;
+    const R c_pl = scalar<R>(sc, SC_CPL), c_rt = scalar<R>(sc, SC_CRT), c_cb = scalar<R>(sc, SC_CCB);
+    const Coord c = swept_site(sw, j);
+    const int64_t k = index_of(g, c);
+    const int64_t kp = k + disp(g, c, rho, 1), km = k + disp(g, c, rho, -1);
+    const int base = rho * 6;
 
-        // plaquettes and the two rectangle chains along rho
-        Mat<R> t;
-        R tr_pl = R(0);
-        {
-            Mat<R> pl, p1, p2;
-            set_zero(pl);
-            set_zero(p1);
-            set_zero(p2);
+    // plaquettes and the two rectangle chains along rho
+    Mat<R> t;
+    R tr_pl = R(0);
+    {
+        Mat<R> pl, p1, p2;
+        set_zero(pl);
+        set_zero(p1);
+        set_zero(p2);
 #pragma unroll 1
-            for (int j = 0; j < 6; ++j) {
-                const Mat<R> s = load_link(sf, g.V, base + j, k);
-                add_to(pl, s);
-                mul_acc<N, N>(p1, load_link(sf, g.V, base + j, kp), s);
-                mul_acc<N, N>(p2, s, load_link(sf, g.V, base + j, km));
-            }
-            if constexpr (ACTION) tr_pl = re_trace_mul<N, N>(load_link(links, g.V, rho, k), pl);
-            t = pl;
-            scale(t, c_pl);
-            scale(p1, c_rt);
-            mul_acc<N, N>(t, load_link(links, g.V, rho, kp), p1);
-            scale(p2, c_rt);
-            mul_acc<N, N>(t, p2, load_link(links, g.V, rho, km));
+        for (int jj = 0; jj < 6; ++jj) {
+            const Mat<R> s = load_link(sf, g.V, base + jj, k);
+            add_to(pl, s);
+            mul_acc<N, N>(p1, load_link(sf, g.V, base + jj, kp), s);
+            mul_acc<N, N>(p2, s, load_link(sf, g.V, base + jj, km));
         }
-
-        // everything that starts with link(k+rho, d): cubes and the rectangle
-        // along d; positive and negative d in two loops, each with one small
-        // body (the orientation of the shared links is fixed at compile time)
+        if constexpr (ACTION) tr_pl = re_trace_mul<N, N>(load_link(links, g.V, rho, k), pl);
+        t = pl;
+        scale(t, c_pl);
+        scale(p1, c_rt);
+        mul_acc<N, N>(t, load_link(links, g.V, rho, kp), p1);
+        scale(p2, c_rt);
+        mul_acc<N, N>(t, p2, load_link(links, g.V, rho, km));
+    }
+    // cubes and the rectangles along d: positive, then negative d
 #pragma unroll 1
-        for (int id = 0; id < 3; ++id)
-            d_terms<false, UNROLLQ>(t, links, sf, g, c, rho, k, kp, id, c_rt, c_cb);
+    for (int id = 0; id < 3; ++id) d_terms<false, UNROLLQ>(t, links, sf, g, c, rho, k, kp, id, c_rt, c_cb);
 #pragma unroll 1
-        for (int id = 0; id < 3; ++id)
-            d_terms<true, UNROLLQ>(t, links, sf, g, c, rho, k, kp, id, c_rt, c_cb);
+    for (int id = 0; id < 3; ++id) d_terms<true, UNROLLQ>(t, links, sf, g, c, rho, k, kp, id, c_rt, c_cb);
 
-        const Mat<R> u = load_link(links, g.V, rho, k);
-        const Mat<R> m = mul<N, N>(u, t);
-        R f[8];
-        ta_components(m, scalar<R>(a, SC_BETA6), f);
-        if (a.force != nullptr) store_algebra(static_cast<R *>(a.force), g.V, rho, k, f);
-        if (a.mom != nullptr) {
-            R *mom = static_cast<R *>(a.mom);
-            R p[8];
-            load_algebra(mom, g.V, rho, k, p);
-            const R dt = scalar<R>(a, SC_DT);
+    const Mat<R> m = mul<N, N>(load_link(links, g.V, rho, k), t);
+    R f[8];
+    ta_components(m, scalar<R>(sc, SC_BETA6), f);
+    if (L.force != nullptr) store_algebra(static_cast<R *>(L.force), g.V, rho, k, f);
+    if (L.mom != nullptr) {
+        R *mom = static_cast<R *>(L.mom);
+        R p[8];
+        load_algebra(mom, g.V, rho, k, p);
+        const R dt = scalar<R>(sc, SC_DT);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) p[q] = fma(dt, f[q], p[q]);
-            store_algebra(mom, g.V, rho, k, p);
-        }
-        if constexpr (ACTION) {
-            // this link's share of the action, formed in the working precision
-            // (its rounding is that of the traces themselves) and summed in FP64
-            const R tr_t = m.re[0][0] + m.re[1][1] + m.re[2][2];
-            acc += (double)(act_const - tr_t * R(1.0 / 6.0) - act_cpl * tr_pl);
-        }
+        for (int q = 0; q < 8; ++q) p[q] = fma(dt, f[q], p[q]);
+        store_algebra(mom, g.V, rho, k, p);
     }
     if constexpr (ACTION) {
-        const double s = block_sum_b(acc);
-        if (threadIdx.x == 0) a.partials[blockIdx.x] = s;
+        const R tr_t = m.re[0][0] + m.re[1][1] + m.re[2][2];
+        return (double)(scalar<R>(sc, SC_ACT) - tr_t * R(1.0 / 6.0) - scalar<R>(sc, SC_ACTPL) * tr_pl);
     }
+    return 0.0;
 }
 
-// ------------------------------------------------------ pass B, pipelined
-//
-// The same arithmetic as force_from_staples, with every operand streamed into
-// shared memory by cp.async before it is needed.  Pass B has no reuse that a
-// block could stage (the staples of one site fill 1152 B, so a halo'd tile
-// does not fit), and its loads are scattered gathers that each thread issues
-// for itself; the limiter is their latency.  Each thread therefore walks its
-// 88 operands in 26 groups of at most 4 matrices and keeps NST groups in
-// flight in a ring of shared-memory slots that only it reads: group g + NST-1
-// is requested before group g is used.  Within a thread the ring needs no
-// barrier: cp.async.wait_group orders the copies before the reads, and a slot
-// is refilled only after the instructions that used its previous contents
-// have issued.
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+template <typename R, bool ACTION, bool UNROLLQ>
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? (ACTION ? 3 : 4) : 2)
+    force_from_staples(const __grid_constant__ SfLattice L, const __grid_constant__ KernelScalars sc)
 {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit()
-{
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-
-template <int NPEND> __device__ __forceinline__ void cp_async_wait()
-{
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
-}
-
-constexpr int kGroups = 26;
-
-// Shared-memory ring of one thread: lane q of matrix m in stage st at
-// base[((st * 4 + m) * LQ + q) * blockDim.x].
-template <typename R> struct Ring {
-    using V4 = typename Vec<R>::type;
-    static constexpr int LQ = 12 / Vec<R>::W;
-    V4 *base;
-
-    __device__ __forceinline__ V4 *slot(int st, int m) const
-    {
-        return base + ((st * 4 + m) * LQ) * blockDim.x;
-    }
-    // request matrix `plane` (link or staple plane) at `site` into (st, m)
-    __device__ __forceinline__ void fetch(int st, int m, const R *arr, int64_t V, int plane,
-                                          int64_t site) const
-    {
-        const V4 *src = reinterpret_cast<const V4 *>(arr) + (int64_t)plane * LQ * V + site;
-        V4 *dst = slot(st, m);
-#pragma unroll
-        for (int q = 0; q < LQ; ++q) cp_async16(dst + q * blockDim.x, src + q * V);
-    }
-    __device__ __forceinline__ Mat<R> read(int st, int m) const
-    {
-        const V4 *src = slot(st, m);
-        R r[12];
-#pragma unroll
-        for (int q = 0; q < LQ; ++q) {
-            const V4 v = src[q * blockDim.x];
-            if constexpr (Vec<R>::W == 4) {
-                r[4 * q + 0] = v.x;
-                r[4 * q + 1] = v.y;
-                r[4 * q + 2] = v.z;
-                r[4 * q + 3] = v.w;
-            } else {
-                r[2 * q + 0] = v.x;
-                r[2 * q + 1] = v.y;
-            }
+    const Geom g = make_geom(L.dims);
+    const Sweep sw = make_sweep(L, g);
+    const int64_t nvb = virtual_blocks(g.V);
+    for (int64_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+        const double acc = force_block<R, ACTION, UNROLLQ>(L, sc, g, sw, vb);
+        if constexpr (ACTION) {
+            const double s = block_sum(acc);
+            if (threadIdx.x == 0) L.partials[vb] = s;
         }
-        Mat<R> u;
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                u.re[i][j] = r[6 * i + 2 * j];
-                u.im[i][j] = r[6 * i + 2 * j + 1];
-            }
-        rebuild_row2(u);
-        return u;
     }
-};
+}
 
-struct LinkSite {
-    int rho;
-    int64_t k, kp, km;
-    Coord c;
-};
+template <typename R, bool ACTION, bool UNROLLQ>
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? (ACTION ? 3 : 4) : 2)
+    force_from_staples_batched(const __grid_constant__ SfBatch B,
+                               const __grid_constant__ KernelScalars sc)
+{
+    for (int64_t vb = next_virtual_block(B.counter + 1); vb < B.total;
+         vb = next_virtual_block(B.counter + 1)) {
+        const int c = batch_entry(B, vb);
+        const SfLattice &L = B.e[c];
+        const Geom g = make_geom(L.dims);
+        const double acc = force_block<R, ACTION, UNROLLQ>(L, sc, g, make_sweep(L, g), vb - L.vb_begin);
+        if constexpr (ACTION) {
+            const double s = block_sum(acc);
+            if (threadIdx.x == 0) L.partials[vb - L.vb_begin] = s;
+        }
+    }
+}
 
-// Request the operands of group g of link L into stage st (g past the end:
-// an empty group, so that the group count stays uniform).
-//   g 0..5   S_j(k), S_j(k+rho), S_j(k-rho)               (plaquettes, rectangle chains)
-//   g 6      U_rho(k), U_rho(k+rho), U_rho(k-rho)
-//   g 7..24  per d = 0..5: two cube groups (S^{(rho)}_b(k+d), S^{(d)}_b(k) for the two
-//            signs of one b direction), then S_d(k+d), link(k, d), link(k+rho, d)
-//   g 25     U_rho(k)
+// One block per lattice of a batch: its action from its partial sums, in the
+// order and grouping of finish_sum, so batched and single results agree.
+__global__ void __launch_bounds__(1024) finish_batched(const __grid_constant__ SfBatch B, double scale)
+{
+    const SfLattice &L = B.e[blockIdx.x];
+    if (L.action == nullptr) return;
+    const int count = (int)virtual_blocks(make_geom(L.dims).V);
+    __shared__ double warp_part[32];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < count; i += 1024) v += L.partials[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) warp_part[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double s = warp_part[lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) *L.action = scale * s;
+    }
+}
+
+unsigned grid_of(int64_t items)
+{
+    if (items < 1) items = 1;
+    if (items > ((int64_t)1 << 30)) items = (int64_t)1 << 30;
+    return (unsigned)items;
+}
+
+// Pass-B schedules (same arithmetic, different traversal):
+//   0  micro-tiles 8x2x2, inner b loop rolled
+//   1  micro-tiles 8x2x2, inner b loop unrolled
+//   2  x rows (no micro-tiles), inner b loop rolled
+// The process-wide choice per precision is set by lqcd_set_force_variant or
+// lqcd_autotune_force; -1 means the default.
+constexpr int kSfVariants = 3;
+constexpr int kSfDefault = 2;
+std::atomic<int> g_sf_variant[2] = {{-1}, {-1}};
+
+// Largest divisor of L not above cap.
+int block_extent(int L, int cap)
+{
+    for (int b = cap < L ? cap : L; b > 1; --b)
+        if (L % b == 0) return b;
+    return 1;
+}
+
+void set_traversal(SfLattice &L, int variant)
+{
+    L.sweep[0] = block_extent(L.dims[0], 64);
+    L.sweep[1] = block_extent(L.dims[1], 16);
+    L.sweep[2] = block_extent(L.dims[2], 16);
+    if (variant == 2) {
+        L.micro[0] = L.sweep[0];
+        L.micro[1] = L.micro[2] = 1;
+    } else {
+        L.micro[0] = block_extent(L.sweep[0], 8);
+        L.micro[1] = L.sweep[1] % 2 == 0 ? 2 : 1;
+        L.micro[2] = L.sweep[2] % 2 == 0 ? 2 : 1;
+    }
+}
+
+KernelScalars make_scalars(const ForceArgs &a)
+{
+    KernelScalars k;
+    const double sc[7] = {a.beta / 6.0, a.c_plaq, a.c_rect, a.c_cube,
+                          3.0 * (1.5 * a.c_plaq + 3.0 * a.c_rect + 4.0 * a.c_cube), a.c_plaq / 12.0,
+                          a.dt};
+    for (int i = 0; i < 7; ++i) {
+        k.d[i] = sc[i];
+        k.f[i] = (float)sc[i];
+    }
+    return k;
+}
+
+int resolve_variant(const ForceArgs &a)
+{
+    if (a.variant >= 0 && a.variant < kSfVariants) return a.variant;
+    const int v = g_sf_variant[a.precision == LQCD_F64 ? 1 : 0].load();
+    return v < 0 ? kSfDefault : v;
+}
+
+// CTAs of a persistent launch: as many as are resident on the device at
+// once (occupancy of the kernel times the SM count, cached per device).
+template <typename K> unsigned persistent_grid(K kernel, int slot, int64_t work)
+{
+    static std::mutex mu;
+    static int cached[64][8] = {{0}};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return grid_of(work);
+    int resident = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (cached[dev][slot] == 0) {
+            int sms = 0, per_sm = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
+            cached[dev][slot] = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+        }
+        resident = cached[dev][slot];
+    }
+    return grid_of(work < resident ? work : resident);
+}
+
+template <typename R, bool ACTION>
+cudaError_t launch_pass_b(const SfLattice &L, const KernelScalars &sc, int variant, cudaStream_t st)
+{
+    const unsigned grid = grid_of(virtual_blocks((int64_t)L.dims[0] * L.dims[1] * L.dims[2] * L.dims[3]));
+    if (variant == 1) force_from_staples<R, ACTION, true><<<grid, kBlock, 0, st>>>(L, sc);
+    else force_from_staples<R, ACTION, false><<<grid, kBlock, 0, st>>>(L, sc);
+    return cudaGetLastError();
+}
+
+template <typename R, bool ACTION>
+cudaError_t launch_pass_b_batched(const SfBatch &B, const KernelScalars &sc, int variant,
+                                  cudaStream_t st)
+{
+    const int slot = (sizeof(R) == 8 ? 4 : 0) + (ACTION ? 2 : 0) + (variant == 1 ? 1 : 0);
+    if (variant == 1) {
+        auto k = force_from_staples_batched<R, ACTION, true>;
+        k<<<persistent_grid(k, slot, B.total), kBlock, 0, st>>>(B, sc);
+    } else {
+        auto k = force_from_staples_batched<R, ACTION, false>;
+        k<<<persistent_grid(k, slot, B.total), kBlock, 0, st>>>(B, sc);
+    }
+    return cudaGetLastError();
+}
+
+template <typename R> cudaError_t launch_sf_t(const ForceArgs &a, cudaStream_t st)
+{
+    const int variant = resolve_variant(a);
+    SfLattice L{};
+    for (int i = 0; i < 4; ++i) L.dims[i] = a.dims[i];
+    set_traversal(L, variant);
+    L.links = a.links;
+    L.staples = a.staples;
+    L.force = a.force;
+    L.mom = a.mom;
+    L.partials = a.partials;
+    L.action = a.action;
+    const KernelScalars sc = make_scalars(a);
+    const int64_t nvb = virtual_blocks((int64_t)a.dims[0] * a.dims[1] * a.dims[2] * a.dims[3]);
+    staple_fields<R><<<grid_of(nvb), kBlock, 0, st>>>(L);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (a.action != nullptr) {
+        e = launch_pass_b<R, true>(L, sc, variant, st);
+        if (e != cudaSuccess) return e;
+        return launch_finish_sum(a.partials, (int)nvb, a.beta / 3.0, a.action, st);
+    }
+    return launch_pass_b<R, false>(L, sc, variant, st);
+}
+
 template <typename R>
-__device__ __forceinline__ void issue_group(const Ring<R> &ring, int st, int g, const R *links,
-                                            const R *sf, const Geom &gm, const LinkSite &L)
+cudaError_t launch_sf_batched_t(const ForceArgs &a, int n, const SfLattice *items,
+                                unsigned long long *counter, cudaStream_t st)
 {
-    if (g < kGroups) {
-        const int64_t V = gm.V;
-        const int base = L.rho * 6;
-        if (g < 6) {
-            ring.fetch(st, 0, sf, V, base + g, L.k);
-            ring.fetch(st, 1, sf, V, base + g, L.kp);
-            ring.fetch(st, 2, sf, V, base + g, L.km);
-        } else if (g == 6) {
-            ring.fetch(st, 0, links, V, L.rho, L.k);
-            ring.fetch(st, 1, links, V, L.rho, L.kp);
-            ring.fetch(st, 2, links, V, L.rho, L.km);
-        } else if (g < 25) {
-            const int h = g - 7;
-            const int jd = h / 3, r = h - 3 * (h / 3);
-            const int id = jd >> 1;
-            const int nud = (L.rho + 1 + id) & 3;
-            const bool neg = jd & 1;
-            const int64_t kd = L.k + disp(gm, L.c, nud, neg ? -1 : 1);
-            if (r < 2) {
-                const int ib = r == 0 ? (id == 0 ? 1 : 0) : (id == 2 ? 1 : 2);
-                const int nub = (L.rho + 1 + ib) & 3;
-                const int jp = 2 * ((nub - nud - 1) & 3);
-                const int64_t site2 = neg ? kd : L.k;
-                ring.fetch(st, 0, sf, V, base + 2 * ib, kd);
-                ring.fetch(st, 1, sf, V, nud * 6 + jp, site2);
-                ring.fetch(st, 2, sf, V, base + 2 * ib + 1, kd);
-                ring.fetch(st, 3, sf, V, nud * 6 + jp + 1, site2);
-            } else {
-                ring.fetch(st, 0, sf, V, base + jd, kd);
-                ring.fetch(st, 1, links, V, nud, neg ? kd : L.k);
-                ring.fetch(st, 2, links, V, nud, L.kp + (neg ? kd - L.k : 0));
-            }
-        } else {
-            ring.fetch(st, 0, links, V, L.rho, L.k);
-        }
+    const int variant = resolve_variant(a);
+    SfBatch B{};
+    B.n = n;
+    B.counter = counter;
+    bool any_action = false;
+    int64_t vb = 0;
+    for (int c = 0; c < n; ++c) {
+        B.e[c] = items[c];
+        set_traversal(B.e[c], variant);
+        B.e[c].vb_begin = vb;
+        vb += virtual_blocks((int64_t)items[c].dims[0] * items[c].dims[1] * items[c].dims[2] *
+                             items[c].dims[3]);
+        any_action = any_action || items[c].action != nullptr;
     }
-    cp_async_commit();
-}
-
-template <typename R, bool ACTION, int NST>
-__global__ void __launch_bounds__(kBlockB, sizeof(R) == 4 ? 3 : 2)
-    force_from_staples_async(const ForceArgs a)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Ring<R> ring{reinterpret_cast<typename Vec<R>::type *>(smem_raw) + threadIdx.x};
-    const Geom g = make_geom(a.dims);
-    const R *__restrict__ links = static_cast<const R *>(a.links);
-    const R *__restrict__ sf = static_cast<const R *>(a.staples);
-    const R c_pl = scalar<R>(a, SC_CPL), c_rt = scalar<R>(a, SC_CRT), c_cb = scalar<R>(a, SC_CCB);
-    const R act_const = scalar<R>(a, SC_ACT), act_cpl = scalar<R>(a, SC_ACTPL);
-    const Sweep sw = make_sweep(a, g);
-    // sites padded to whole warps: thread i takes site ((i >> 7) << 5) | (i & 31)
-    // and direction (i >> 5) & 3; padding sites are skipped
-    const int64_t nthreads = 4 * padded_sites(g.V);
-    double acc = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nthreads;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        if ((((i >> 7) << 5) | (i & 31)) >= g.V) continue;
-        LinkSite L;
-        L.rho = (int)((i >> 5) & 3);
-        L.c = swept_site(sw, ((i >> 7) << 5) | (i & 31));
-        L.k = index_of(g, L.c);
-        L.kp = L.k + disp(g, L.c, L.rho, 1);
-        L.km = L.k + disp(g, L.c, L.rho, -1);
-
-        // prologue: NST - 1 groups in flight
-#pragma unroll
-        for (int q = 0; q < NST - 1; ++q) issue_group(ring, q, q, links, sf, g, L);
-        int gi = 0;      // group being consumed
-        int st = 0;      // its stage
-        int st_next = NST - 1;
-        auto advance = [&]() {
-            issue_group(ring, st_next, gi + NST - 1, links, sf, g, L);
-            st_next = st_next + 1 == NST ? 0 : st_next + 1;
-            cp_async_wait<NST - 1>();
-        };
-        auto next = [&]() {
-            ++gi;
-            st = st + 1 == NST ? 0 : st + 1;
-        };
-
-        Mat<R> t;
-        R tr_pl = R(0);
-        {
-            Mat<R> pl, p1, p2;
-            set_zero(pl);
-            set_zero(p1);
-            set_zero(p2);
-#pragma unroll 1
-            for (int j = 0; j < 6; ++j) {
-                advance();
-                const Mat<R> s0 = ring.read(st, 0);
-                add_to(pl, s0);
-                mul_acc<N, N>(p1, ring.read(st, 1), s0);
-                mul_acc<N, N>(p2, s0, ring.read(st, 2));
-                next();
-            }
-            advance();
-            if constexpr (ACTION) tr_pl = re_trace_mul<N, N>(ring.read(st, 0), pl);
-            t = pl;
-            scale(t, c_pl);
-            scale(p1, c_rt);
-            mul_acc<N, N>(t, ring.read(st, 1), p1);
-            scale(p2, c_rt);
-            mul_acc<N, N>(t, p2, ring.read(st, 2));
-            next();
-        }
-#pragma unroll 1
-        for (int jd = 0; jd < 6; ++jd) {
-            const bool neg = jd & 1;
-            Mat<R> y;
-            set_zero(y);
-#pragma unroll 1
-            for (int r = 0; r < 2; ++r) {
-                advance();
-                if (!neg) {
-                    mul_acc<N, N>(y, ring.read(st, 0), ring.read(st, 1));
-                    mul_acc<N, N>(y, ring.read(st, 2), ring.read(st, 3));
-                } else {
-                    mul_acc<N, D>(y, ring.read(st, 0), ring.read(st, 1));
-                    mul_acc<N, D>(y, ring.read(st, 2), ring.read(st, 3));
-                }
-                next();
-            }
-            advance();
-            scale(y, c_cb);
-            Mat<R> r3 = ring.read(st, 0);
-            scale(r3, c_rt);
-            if (!neg) {
-                mul_acc<N, D>(y, r3, ring.read(st, 1));
-                mul_acc<N, N>(t, ring.read(st, 2), y);
-            } else {
-                mul_acc<N, N>(y, r3, ring.read(st, 1));
-                mul_acc<D, N>(t, ring.read(st, 2), y);
-            }
-            next();
-        }
-        advance();
-        const Mat<R> m = mul<N, N>(ring.read(st, 0), t);
-        next();
-
-        R f[8];
-        ta_components(m, scalar<R>(a, SC_BETA6), f);
-        if (a.force != nullptr) store_algebra(static_cast<R *>(a.force), g.V, L.rho, L.k, f);
-        if (a.mom != nullptr) {
-            R *mom = static_cast<R *>(a.mom);
-            R p[8];
-            load_algebra(mom, g.V, L.rho, L.k, p);
-            const R dt = scalar<R>(a, SC_DT);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) p[q] = fma(dt, f[q], p[q]);
-            store_algebra(mom, g.V, L.rho, L.k, p);
-        }
-        if constexpr (ACTION) {
-            // this link's share of the action, formed in the working precision
-            // (its rounding is that of the traces themselves) and summed in FP64
-            const R tr_t = m.re[0][0] + m.re[1][1] + m.re[2][2];
-            acc += (double)(act_const - tr_t * R(1.0 / 6.0) - act_cpl * tr_pl);
-        }
-    }
-    if constexpr (ACTION) {
-        const double s = block_sum_b(acc);
-        if (threadIdx.x == 0) a.partials[blockIdx.x] = s;
-    }
-}
-
-unsigned grid_of(int64_t items, int block)
-{
-    int64_t g = (items + block - 1) / block;
-    if (g < 1) g = 1;
-    if (g > ((int64_t)1 << 30)) g = (int64_t)1 << 30;
-    return (unsigned)g;
+    B.total = vb;
+    const KernelScalars sc = make_scalars(a);
+    cudaError_t e = cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    auto ka = staple_fields_batched<R>;
+    ka<<<persistent_grid(ka, 3 + (sizeof(R) == 8 ? 4 : 0), B.total), kBlock, 0, st>>>(B);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (!any_action) return launch_pass_b_batched<R, false>(B, sc, variant, st);
+    e = launch_pass_b_batched<R, true>(B, sc, variant, st);
+    if (e != cudaSuccess) return e;
+    finish_batched<<<n, 1024, 0, st>>>(B, a.beta / 3.0);
+    return cudaGetLastError();
 }
 
 } // namespace
@@ -567,104 +544,20 @@ size_t staple_field_bytes(const int dims[4], int precision)
 
 int staple_force_partials(const int dims[4])
 {
-    const int64_t V = (int64_t)dims[0] * dims[1] * dims[2] * dims[3];
-    return (int)grid_of(4 * padded_sites(V), kBlockB);
+    return (int)virtual_blocks((int64_t)dims[0] * dims[1] * dims[2] * dims[3]);
 }
 
-// Dynamic shared memory of the pipelined pass B, and its once-per-device
-// opt-in above the 48 KB default.
-template <typename R, int NST> constexpr size_t async_smem_bytes()
+cudaError_t launch_force_staple_fields(const ForceArgs &a, cudaStream_t st)
 {
-    return (size_t)NST * 4 * (12 / Vec<R>::W) * kBlockB * 16;
+    return a.precision == LQCD_F64 ? launch_sf_t<double>(a, st) : launch_sf_t<float>(a, st);
 }
 
-template <typename R, bool ACTION, int NST>
-static cudaError_t launch_async(const ForceArgs &a, unsigned grid, cudaStream_t st)
+cudaError_t launch_force_staple_fields_batched(const ForceArgs &a, int n, const SfLattice *items,
+                                               unsigned long long *counter, cudaStream_t st)
 {
-    constexpr size_t smem = async_smem_bytes<R, NST>();
-    static std::mutex mu;
-    static bool done[64] = {false};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    {
-        std::lock_guard<std::mutex> lk(mu);
-        if (!done[dev]) {
-            e = cudaFuncSetAttribute(force_from_staples_async<R, ACTION, NST>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            done[dev] = true;
-        }
-    }
-    force_from_staples_async<R, ACTION, NST><<<grid, kBlockB, smem, st>>>(a);
-    return cudaGetLastError();
-}
-
-// Largest divisor of L not above cap.
-static int block_extent(int L, int cap)
-{
-    for (int b = cap < L ? cap : L; b > 1; --b)
-        if (L % b == 0) return b;
-    return 1;
-}
-
-// Pass-B variants (same arithmetic, different schedules):
-//   0  micro-tiles 8x2x2, inner b loop rolled
-//   1  micro-tiles 8x2x2, inner b loop unrolled
-//   2  x rows (no micro-tiles), inner b loop rolled
-//   3  micro-tiles 8x2x2, operands streamed through a cp.async ring
-// The process-wide choice per precision is set by lqcd_set_force_variant or
-// lqcd_autotune_force; -1 means the default.
-constexpr int kSfVariants = 4;
-constexpr int kSfDefault = 0;
-static std::atomic<int> g_sf_variant[2] = {{-1}, {-1}};
-
-template <typename R, bool ACTION>
-static cudaError_t launch_pass_b(const ForceArgs &a, unsigned grid, cudaStream_t st)
-{
-    constexpr int NST = sizeof(R) == 4 ? 3 : 2;
-    switch (a.variant) {
-    case 1: force_from_staples<R, ACTION, true><<<grid, kBlockB, 0, st>>>(a); break;
-    case 3: return launch_async<R, ACTION, NST>(a, grid, st);
-    default: force_from_staples<R, ACTION, false><<<grid, kBlockB, 0, st>>>(a); break;
-    }
-    return cudaGetLastError();
-}
-
-template <typename R> static cudaError_t launch_sf_t(const ForceArgs &args, cudaStream_t st)
-{
-    ForceArgs a = args;
-    const double sc[7] = {a.beta / 6.0, a.c_plaq, a.c_rect, a.c_cube,
-                          3.0 * (1.5 * a.c_plaq + 3.0 * a.c_rect + 4.0 * a.c_cube), a.c_plaq / 12.0,
-                          a.dt};
-    for (int i = 0; i < 7; ++i) {
-        a.sc.d[i] = sc[i];
-        a.sc.f[i] = (float)sc[i];
-    }
-    a.sweep[0] = block_extent(a.dims[0], 64);
-    a.sweep[1] = block_extent(a.dims[1], 16);
-    a.sweep[2] = block_extent(a.dims[2], 16);
-    if (a.variant == 2) {
-        a.micro[0] = a.sweep[0];
-        a.micro[1] = a.micro[2] = 1;
-    } else {
-        a.micro[0] = block_extent(a.sweep[0], 8);
-        a.micro[1] = a.sweep[1] % 2 == 0 ? 2 : 1;
-        a.micro[2] = a.sweep[2] % 2 == 0 ? 2 : 1;
-    }
-    const Geom g = make_geom(a.dims);
-    staple_fields<R><<<grid_of(4 * padded_sites(g.V), kBlockA), kBlockA, 0, st>>>(
-        static_cast<const R *>(a.links), static_cast<R *>(a.staples), g);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const unsigned grid = grid_of(4 * padded_sites(g.V), kBlockB);
-    if (a.action != nullptr) {
-        e = launch_pass_b<R, true>(a, grid, st);
-        if (e != cudaSuccess) return e;
-        return launch_finish_sum(a.partials, (int)grid, a.beta / 3.0, a.action, st);
-    }
-    return launch_pass_b<R, false>(a, grid, st);
+    if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
+    return a.precision == LQCD_F64 ? launch_sf_batched_t<double>(a, n, items, counter, st)
+                                   : launch_sf_batched_t<float>(a, n, items, counter, st);
 }
 
 int staple_force_variants() { return kSfVariants; }
@@ -678,13 +571,6 @@ int staple_force_variant(int precision)
 void set_staple_force_variant(int precision, int variant)
 {
     g_sf_variant[precision == LQCD_F64 ? 1 : 0].store(variant);
-}
-
-cudaError_t launch_force_staple_fields(const ForceArgs &args, cudaStream_t st)
-{
-    ForceArgs a = args;
-    if (a.variant < 0 || a.variant >= kSfVariants) a.variant = staple_force_variant(a.precision);
-    return a.precision == LQCD_F64 ? launch_sf_t<double>(a, st) : launch_sf_t<float>(a, st);
 }
 
 } // namespace lqcd

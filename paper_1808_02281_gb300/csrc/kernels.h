@@ -46,11 +46,35 @@ struct ForceArgs {
     void *staples;     // staple-field algorithm: workspace for the 24 staple planes
     double *partials;  // staple-field algorithm with action: per-block partial sums
     double *action;    // staple-field algorithm: action written here when set
-    int sweep[3];      // staple-field force pass: spatial block extents of the traversal
-    int micro[3];      // staple-field force pass: micro-tile extents inside a block slice
     int variant;       // staple-field force pass schedule; -1 = process-wide choice
-    KernelScalars sc;  // filled by the staple-field launcher
 };
+
+// One lattice as the staple-field kernels see it (filled on the host).
+struct SfLattice {
+    int dims[4];
+    int sweep[3];      // spatial block extents of the pass-B traversal
+    int micro[3];      // micro-tile extents inside a block slice
+    int64_t vb_begin;  // batch: first virtual block of this lattice
+    const void *links;
+    void *staples;     // 24 staple planes (workspace)
+    void *force;       // written when set
+    void *mom;         // p += dt f when set
+    double *partials;  // one action partial per virtual block
+    double *action;    // action written here when set
+};
+
+constexpr int kMaxBatch = 64;
+
+struct SfBatch {
+    int n;
+    int64_t total;                 // virtual blocks of all lattices
+    unsigned long long *counter;   // work counters (2, zeroed before the passes)
+    SfLattice e[kMaxBatch];
+};
+
+// Bytes at the end of a batch workspace for the persistent launches' work
+// counters.
+constexpr size_t kBatchCounterBytes = 256;
 
 cudaError_t launch_force(const ForceArgs &a, cudaStream_t st);
 
@@ -59,6 +83,10 @@ cudaError_t launch_force(const ForceArgs &a, cudaStream_t st);
 size_t staple_field_bytes(const int dims[4], int precision);
 int staple_force_partials(const int dims[4]);
 cudaError_t launch_force_staple_fields(const ForceArgs &a, cudaStream_t st);
+// a: precision, coefficients, dt, variant; items: the lattices (their dims,
+// links, staples, force, mom, partials, action), 1 <= n <= kMaxBatch.
+cudaError_t launch_force_staple_fields_batched(const ForceArgs &a, int n, const SfLattice *items,
+                                               unsigned long long *counter, cudaStream_t st);
 int staple_force_variants();
 int staple_force_variant(int precision);
 void set_staple_force_variant(int precision, int variant);
@@ -109,6 +137,14 @@ struct MdArgs {
 };
 
 cudaError_t launch_update_momenta(const MdArgs &a, cudaStream_t st);
+// U <- exp(i dt p.T) U for n lattices in one persistent launch.
+struct LinkStepItem {
+    int64_t V;
+    void *links;
+    const void *mom;
+};
+cudaError_t launch_update_links_batched(int precision, int n, const LinkStepItem *items, double dt,
+                                        cudaStream_t st);
 cudaError_t launch_update_links(const MdArgs &a, cudaStream_t st);
 cudaError_t launch_links_from_omega(const MdArgs &a, cudaStream_t st);
 cudaError_t launch_omega_gradient(const MdArgs &a, cudaStream_t st);

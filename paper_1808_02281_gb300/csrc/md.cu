@@ -92,6 +92,57 @@ __global__ void __launch_bounds__(kBlock) update_links(R *__restrict__ links,
     }
 }
 
+// The link step of update_links for one link of a batch of lattices: the
+// persistent CTAs walk the concatenated link ranges.
+struct LinkBatch {
+    int n;
+    int64_t total;
+    int64_t begin[kMaxBatch + 1]; // first link of each lattice in the concatenation
+    int64_t V[kMaxBatch];
+    void *links[kMaxBatch];
+    const void *mom[kMaxBatch];
+};
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) update_links_batched(const __grid_constant__ LinkBatch B, R dt)
+{
+    int c = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < B.total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        while (c > 0 && i < B.begin[c]) --c;
+        while (c + 1 < B.n && i >= B.begin[c + 1]) ++c;
+        const int64_t V = B.V[c];
+        const int64_t l = i - B.begin[c];
+        const int mu = (int)(l / V);
+        const int64_t n = l - mu * V;
+        R *links = static_cast<R *>(B.links[c]);
+        R p[8];
+        load_algebra(static_cast<const R *>(B.mom[c]), V, mu, n, p);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) p[q] *= dt;
+        const Mat<R> e = exp_i_hermitian(algebra_matrix(p));
+        const Mat<R> v = load_link(links, V, mu, n);
+        Mat<R> u;
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                R re = R(0), im = R(0);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    re = fma(e.re[r][k], v.re[k][j], re);
+                    re = fma(-e.im[r][k], v.im[k][j], re);
+                    im = fma(e.re[r][k], v.im[k][j], im);
+                    im = fma(e.im[r][k], v.re[k][j], im);
+                }
+                u.re[r][j] = re;
+                u.im[r][j] = im;
+            }
+        reunitarise(u);
+        store_link(links, V, mu, n, u);
+    }
+}
+
 // Chain rule through U = exp(X) U0, X = i W, W = omega.T (Eq. 18_1_29_3).
 // A change d omega moves U by the left perturbation exp(i delta.T) with
 // i delta.T = phi(ad_X)(i d omega.T), phi(z) = (e^z - 1)/z.  The force gives
@@ -257,6 +308,35 @@ cudaError_t launch_update_links(const MdArgs &a, cudaStream_t st)
     else
         update_links<float, false><<<grid_for(4 * V), kBlock, 0, st>>>(
             static_cast<float *>(a.links), static_cast<const float *>(a.mom), V, (float)a.dt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_links_batched(int precision, int n, const LinkStepItem *items, double dt,
+                                        cudaStream_t st)
+{
+    if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
+    LinkBatch B{};
+    B.n = n;
+    int64_t pos = 0;
+    for (int c = 0; c < n; ++c) {
+        B.begin[c] = pos;
+        B.V[c] = items[c].V;
+        B.links[c] = items[c].links;
+        B.mom[c] = items[c].mom;
+        pos += 4 * items[c].V;
+    }
+    B.begin[n] = pos;
+    B.total = pos;
+    int dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t grid = (pos + kBlock - 1) / kBlock;
+    const int64_t cap = (int64_t)(sms > 0 ? sms : 1) * 8;
+    if (grid > cap) grid = cap;
+    if (grid < 1) grid = 1;
+    if (precision == LQCD_F64)
+        update_links_batched<double><<<(unsigned)grid, kBlock, 0, st>>>(B, dt);
+    else
+        update_links_batched<float><<<(unsigned)grid, kBlock, 0, st>>>(B, (float)dt);
     return cudaGetLastError();
 }
 

@@ -120,6 +120,87 @@ class GraphTrajectory:
         self.graph.replay()
 
 
+@dataclasses.dataclass
+class BatchState:
+    """Many lattices (uneven extents, one precision and action) advanced
+    together: every kick and drift is one launch per pass for all of them."""
+    params: lqcd.Lattice
+    dims: list
+    links: list
+    mom: list
+    workspace: torch.Tensor
+
+    @classmethod
+    def create(cls, params: lqcd.Lattice, dims, links, mom) -> "BatchState":
+        dims = [tuple(d) for d in dims]
+        return cls(params, dims, list(links), list(mom),
+                   lqcd.make_workspace_batched(params, dims, links[0].device))
+
+    def clone(self) -> "BatchState":
+        return BatchState(self.params, self.dims, [u.clone() for u in self.links],
+                          [p.clone() for p in self.mom], self.workspace)
+
+
+def batch_kick(bs: BatchState, coef: float) -> None:
+    lqcd.md_force_step_batched(bs.params, bs.dims, bs.links, mom=bs.mom, dt=coef,
+                               workspace=bs.workspace)
+
+
+def batch_drift(bs: BatchState, coef: float) -> None:
+    lqcd.md_update_links_batched(bs.params, bs.dims, bs.links, bs.mom, coef)
+
+
+def batch_leapfrog(bs: BatchState, dt: float, nsteps: int) -> None:
+    batch_kick(bs, dt / 2)
+    for i in range(nsteps):
+        batch_drift(bs, dt)
+        batch_kick(bs, dt if i < nsteps - 1 else dt / 2)
+
+
+def batch_omelyan(bs: BatchState, dt: float, nsteps: int, lam: float = OMELYAN_LAMBDA) -> None:
+    batch_kick(bs, lam * dt)
+    for i in range(nsteps):
+        batch_drift(bs, dt / 2)
+        batch_kick(bs, (1 - 2 * lam) * dt)
+        batch_drift(bs, dt / 2)
+        batch_kick(bs, 2 * lam * dt if i < nsteps - 1 else lam * dt)
+
+
+BATCH_INTEGRATORS = {"leapfrog": batch_leapfrog, "omelyan": batch_omelyan}
+
+
+class GraphBatchTrajectory:
+    """A batch trajectory captured as one CUDA graph (replay() advances the
+    tensors of ``bs`` in place)."""
+
+    def __init__(self, bs: BatchState, dt: float, nsteps: int, integrator: str = "leapfrog"):
+        self.bs = bs
+        run = BATCH_INTEGRATORS[integrator]
+        scratch = bs.clone()
+        run(scratch, dt, 1)
+        torch.cuda.synchronize()
+        del scratch
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            run(bs, dt, nsteps)
+
+    def replay(self) -> None:
+        self.graph.replay()
+
+
+def initial_batch(dims_list, precision: str, sigma: float = 0.3, u0: float = 0.87,
+                  beta: float = 6.0, seed: int = 0, device="cuda") -> BatchState:
+    """One seeded lattice and momentum field per entry (seed + 2 * index)."""
+    params = lqcd.Lattice.symanzik(dims_list[0], beta, u0, precision)
+    links, mom = [], []
+    for c, dims in enumerate(dims_list):
+        lat = params.with_(dims=tuple(dims))
+        links.append(lqcd.links_from_omega(
+            lat, lqcd.algebra_to_device(lat, synth.omega(dims, sigma, seed + 2 * c), device)))
+        mom.append(lqcd.algebra_to_device(lat, synth.momenta(dims, seed + 2 * c + 1), device))
+    return BatchState.create(params, dims_list, links, mom)
+
+
 def initial_state(dims, precision: str, sigma: float = 0.3, u0: float = 0.87,
                   beta: float = 6.0, seed: int = 0, device="cuda") -> MDState:
     """Links exp(i w.T), w ~ N(0, sigma^2) and Gaussian momenta, both from the

@@ -43,6 +43,15 @@ class Desc(ctypes.Structure):
                 ("c_cube", ctypes.c_double)]
 
 
+MAX_BATCH = 64
+
+
+class LatticeRef(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int32 * 4), ("reserved", ctypes.c_int32 * 4),
+                ("links", ctypes.c_void_p), ("mom", ctypes.c_void_p),
+                ("force", ctypes.c_void_p), ("action", ctypes.c_void_p)]
+
+
 _LIB = None
 _EXPORTS = {
     "lqcd_symanzik_coefficients": (ctypes.c_int, [ctypes.c_double] + [ctypes.POINTER(ctypes.c_double)] * 4),
@@ -73,6 +82,14 @@ _EXPORTS = {
     "lqcd_pack_links": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "lqcd_unpack_links": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "lqcd_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(Desc)]),
+    "lqcd_workspace_bytes_batched": (ctypes.c_size_t, [ctypes.POINTER(Desc), ctypes.c_int,
+                                                       ctypes.POINTER(LatticeRef)]),
+    "lqcd_md_force_step_batched": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_int, ctypes.POINTER(LatticeRef),
+                                                  ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t,
+                                                  ctypes.c_void_p]),
+    "lqcd_md_update_links_batched": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_int,
+                                                    ctypes.POINTER(LatticeRef), ctypes.c_double,
+                                                    ctypes.c_void_p]),
     "lqcd_force_variant_count": (ctypes.c_int, [ctypes.POINTER(Desc)]),
     "lqcd_get_force_variant": (ctypes.c_int, [ctypes.POINTER(Desc)]),
     "lqcd_set_force_variant": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_int]),
@@ -371,6 +388,66 @@ def unpack_links(lat: Lattice, links: torch.Tensor, out: torch.Tensor | None = N
     d = lat.desc()
     _call("lqcd_unpack_links", ctypes.byref(d), _ptr(links), _ptr(out), _stream(stream))
     return out
+
+
+# ---------------------------------------------------------------- batches
+
+def _batch_refs(params: Lattice, dims_list, links=None, mom=None, force=None, actions=None):
+    n = len(dims_list)
+    if not 1 <= n <= MAX_BATCH:
+        raise ValueError(f"a batch holds 1..{MAX_BATCH} lattices")
+    refs = (LatticeRef * n)()
+    for c, dims in enumerate(dims_list):
+        lat = params.with_(dims=tuple(int(d) for d in dims))
+        for i in range(4):
+            refs[c].dims[i] = int(dims[i])
+        if links is not None:
+            _check(links[c], lat, lat.link_shape, f"links[{c}]")
+            refs[c].links = links[c].data_ptr()
+        if mom is not None and mom[c] is not None:
+            _check(mom[c], lat, lat.algebra_shape, f"mom[{c}]")
+            refs[c].mom = mom[c].data_ptr()
+        if force is not None and force[c] is not None:
+            _check(force[c], lat, lat.algebra_shape, f"force[{c}]")
+            refs[c].force = force[c].data_ptr()
+        if actions is not None:
+            refs[c].action = actions.data_ptr() + 8 * c
+    return refs
+
+
+def workspace_bytes_batched(params: Lattice, dims_list) -> int:
+    refs = _batch_refs(params, dims_list)
+    for r in refs:
+        r.links = 16  # the size query checks pointers for presence only
+    d = params.desc()
+    return int(_lib().lqcd_workspace_bytes_batched(ctypes.byref(d), len(dims_list), refs))
+
+
+def make_workspace_batched(params: Lattice, dims_list, device=None) -> torch.Tensor:
+    n = max(workspace_bytes_batched(params, dims_list), 256)
+    return torch.empty(n, dtype=torch.uint8, device=device or "cuda")
+
+
+def md_force_step_batched(params: Lattice, dims_list, links, mom=None, dt: float = 0.0,
+                          force=None, actions: torch.Tensor | None = None,
+                          workspace: torch.Tensor | None = None, stream=None):
+    """Force step of many lattices (extents dims_list, parameters of
+    ``params``) in one launch per pass; actions: float64 device tensor [n]."""
+    if actions is not None and (actions.dtype != torch.float64 or not actions.is_cuda
+                                or actions.numel() != len(dims_list)):
+        raise TypeError("actions must be a float64 CUDA tensor with one entry per lattice")
+    refs = _batch_refs(params, dims_list, links, mom, force, actions)
+    ws = make_workspace_batched(params, dims_list, links[0].device) if workspace is None else workspace
+    d = params.desc()
+    _call("lqcd_md_force_step_batched", ctypes.byref(d), len(dims_list), refs, float(dt), _ptr(ws),
+          ws.numel(), _stream(stream))
+
+
+def md_update_links_batched(params: Lattice, dims_list, links, mom, dt: float, stream=None):
+    refs = _batch_refs(params, dims_list, links, mom)
+    d = params.desc()
+    _call("lqcd_md_update_links_batched", ctypes.byref(d), len(dims_list), refs, float(dt),
+          _stream(stream))
 
 
 def force_variant_count(lat: Lattice) -> int:

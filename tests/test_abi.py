@@ -134,3 +134,27 @@ def test_layout_marshalling_roundtrip():
         for n, mu, c in [(0, 0, 0), (5, 2, 7), (11, 3, 3)]:
             assert flat[((mu * (8 // W) + c // W) * lat.V + n) * W + c % W] == a[n, mu, c]
         np.testing.assert_array_equal(lqcd.algebra_from_device(t), a)
+
+
+def test_batch_argument_checks(lib):
+    d = _desc()
+    refs = (lqcd.LatticeRef * 2)()
+    for r in refs:
+        for i in range(4):
+            r.dims[i] = 4
+        r.links = 0x10000
+        r.mom = 0x20000
+    assert lib.lqcd_md_force_step_batched(ctypes.byref(d), 0, refs, 0.1, GOOD, 1 << 30, None) == -1
+    assert lib.lqcd_md_force_step_batched(ctypes.byref(d), 65, refs, 0.1, GOOD, 1 << 30, None) == -1
+    refs[1].dims[2] = 0
+    assert lib.lqcd_md_force_step_batched(ctypes.byref(d), 2, refs, 0.1, GOOD, 1 << 30, None) == -2
+    refs[1].dims[2] = 4
+    refs[1].mom = 0x20008
+    assert lib.lqcd_md_force_step_batched(ctypes.byref(d), 2, refs, 0.1, GOOD, 1 << 30, None) == -3
+    refs[1].mom = 0x20000
+    dp = _desc(force_algo=1)
+    assert lib.lqcd_md_force_step_batched(ctypes.byref(dp), 2, refs, 0.1, GOOD, 1 << 30, None) == -6
+    assert lib.lqcd_md_force_step_batched(ctypes.byref(d), 2, refs, 0.1, GOOD, 16, None) == -4
+    need = lib.lqcd_workspace_bytes_batched(ctypes.byref(d), 2, refs)
+    assert need == 2 * lib.lqcd_workspace_bytes_batched(ctypes.byref(d), 1, refs) - 256
+    assert need >= 2 * 24 * 12 * 256 * 4
