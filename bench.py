@@ -194,6 +194,51 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------- replicas on N ranks
+
+class RankContext:
+    """One process per GPU (torchrun): replicas of the workload, no data-path
+    collective; only barriers and the max-over-ranks of timings."""
+
+    def __init__(self, backend: str = "nccl"):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.dist = None
+        self.backend = backend
+        if self.world > 1:
+            import torch.distributed as dist
+            if not dist.is_initialized():
+                dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max_over_ranks(self, x: float, device=None) -> float:
+        if self.dist is None:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=device or "cpu")
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+
+
+def replica_seed(seed: int, rank: int) -> int:
+    """Each rank draws its own lattice (the same workload, another sample)."""
+    return seed + rank
+
+
+def weak_scaling_value(links_per_rank: int, world: int, steps: int, ms_max: float) -> float:
+    """Links of all ranks per second (Glink/s) over the slowest rank's time."""
+    return world * links_per_rank * steps / (ms_max / 1e3) / 1e9
+
+
 # ----------------------------------------------------------------- GPU arm
 
 def run_ours(args):
@@ -202,30 +247,22 @@ def run_ours(args):
     from paper_1808_02281_gb300 import build as B
     from paper_1808_02281_gb300 import lqcd, synth
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    ctx = RankContext("nccl")
+    world, rank, local = ctx.world, ctx.rank, ctx.local
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if rank == 0:
         B.build()
-    if dist is not None:
-        dist.barrier()
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
+    ctx.barrier()
+    barrier = ctx.barrier
 
     w = synth.WORKLOADS[WORKLOAD]
     dims = w["dims"]
     V = synth.volume(dims)
     nlinks = 4 * V
-    omega_np = synth.omega(dims, w["sigma"], w["seed"] + rank)
-    p_np = synth.momenta(dims, seed=1000 + rank)
+    seed = replica_seed(w["seed"], rank)
+    omega_np = synth.omega(dims, w["sigma"], seed)
+    p_np = synth.momenta(dims, seed=1000 + seed)
     stream = torch.cuda.current_stream(dev)
     launches = {"n": 0}
 
@@ -284,18 +321,14 @@ def run_ours(args):
         return ms, per, n_launch, S_val
 
     def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return ctx.max_over_ranks(x, dev)
 
     # headline: FP32
     with ClockSampler(local) as clk:
         ms, per, n_launch, S32 = timed("f32", args.steps, args.warmup, True)
     ms = max_over_ranks(ms)
     clocks = clk.summary()
-    value = world * nlinks * args.steps / (ms / 1e3) / 1e9
+    value = weak_scaling_value(nlinks, world, args.steps, ms)
     # FP64 beside it (fewer steps: the FP64 pipe is narrow on this part)
     k64 = max(2, min(args.steps, 5))
     ms64, per64, _, S64 = timed("f64", k64, max(3, min(args.warmup, 3)), True)
@@ -330,20 +363,20 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     e_ms = max_over_ranks(e_start.elapsed_time(e_stop))
     del U, mom, force, S, ws
-    e2e_value = world * nlinks * K_e2e / (e_ms / 1e3) / 1e9
+    e2e_value = weak_scaling_value(nlinks, world, K_e2e, e_ms)
 
     # dH of one Omelyan trajectory (tau 0.5, dt 0.05) from the same draws in
     # FP32 and FP64, H = K + S in FP64 (FP64 action of the FP32-stored links)
     from paper_1808_02281_gb300 import hmc
     dh = {"integrator": "omelyan", "tau": 0.5, "dt": 0.05, "dims": list(dims)}
     for prec in ("f32", "f64"):
-        st = hmc.initial_state(dims, prec, w["sigma"], w["u0"], w["beta"], w["seed"] + rank)
+        st = hmc.initial_state(dims, prec, w["sigma"], w["u0"], w["beta"], seed)
         dh[prec] = hmc.trajectory(st, 0.5, 0.05, "omelyan", action_precision="f64")
         del st
         torch.cuda.empty_cache()
     dh["abs_err_f32"] = abs(dh["f32"] - dh["f64"])
     # the same FP32 trajectory captured as one CUDA graph, replayed
-    st = hmc.initial_state(dims, "f32", w["sigma"], w["u0"], w["beta"], w["seed"] + rank)
+    st = hmc.initial_state(dims, "f32", w["sigma"], w["u0"], w["beta"], seed)
     g_traj = hmc.GraphTrajectory(st, 0.05, 10, "omelyan")
     g_traj.replay()
     torch.cuda.synchronize(dev)
@@ -362,7 +395,7 @@ def run_ours(args):
     torch.cuda.empty_cache()
 
     # uneven-volume batch: 4 each of 8^4, 12^3x24, 16^3x32, 24^3x48 (FP32)
-    bs = hmc.initial_batch(synth.BATCH_DIMS, "f32", w["sigma"], w["u0"], w["beta"], w["seed"] + rank)
+    bs = hmc.initial_batch(synth.BATCH_DIMS, "f32", w["sigma"], w["u0"], w["beta"], seed)
     nl_batch = sum(4 * synth.volume(d) for d in bs.dims)
     actions = torch.empty(len(bs.dims), dtype=torch.float64, device=dev)
 
@@ -405,8 +438,7 @@ def run_ours(args):
     torch.cuda.empty_cache()
 
     if rank != 0:
-        if dist is not None:
-            dist.destroy_process_group()
+        ctx.close()
         return 0
 
     hbm_peak, peak_kind = _peaks()
@@ -453,7 +485,7 @@ def run_ours(args):
         "autotune": tuned,
         "force_glinks": nlinks / (force_ms / 1e3) / 1e9,
         "force_ms": force_ms,
-        "f64": {"value": world * nlinks * k64 / (ms64 / 1e3) / 1e9, "unit": "Glink/s",
+        "f64": {"value": weak_scaling_value(nlinks, world, k64, ms64), "unit": "Glink/s",
                 "ms_per_step": ms64 / k64, "force_ms": per64["force"],
                 "force_glinks": nlinks / (per64["force"] / 1e3) / 1e9, "steps": k64},
         "action_f32": S32, "action_f64": S64,
@@ -468,8 +500,7 @@ def run_ours(args):
         "clocks": clocks,
     }
     print(json.dumps(out))
-    if dist is not None:
-        dist.destroy_process_group()
+    ctx.close()
     return 0
 
 
