@@ -312,8 +312,15 @@ __device__ __forceinline__ double force_block(const SfLattice &L, const KernelSc
     return 0.0;
 }
 
-template <typename R, bool ACTION, bool UNROLLQ>
-__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? (ACTION ? 3 : 4) : 2)
+// Resident CTAs per SM the register allocation aims at: 4 (128 registers)
+// unless the fused action asks for more registers (3) -- or DENSE forces 4.
+template <typename R, bool ACTION, bool DENSE> constexpr int min_blocks()
+{
+    return sizeof(R) == 8 ? 2 : ((ACTION && !DENSE) ? 3 : 4);
+}
+
+template <typename R, bool ACTION, bool UNROLLQ, bool DENSE = false>
+__global__ void __launch_bounds__(kBlock, (min_blocks<R, ACTION, DENSE>()))
     force_from_staples(const __grid_constant__ SfLattice L, const __grid_constant__ KernelScalars sc)
 {
     const Geom g = make_geom(L.dims);
@@ -328,8 +335,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? (ACTION ? 3 : 4) : 2)
     }
 }
 
-template <typename R, bool ACTION, bool UNROLLQ>
-__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? (ACTION ? 3 : 4) : 2)
+template <typename R, bool ACTION, bool UNROLLQ, bool DENSE = false>
+__global__ void __launch_bounds__(kBlock, (min_blocks<R, ACTION, DENSE>()))
     force_from_staples_batched(const __grid_constant__ SfBatch B,
                                const __grid_constant__ KernelScalars sc)
 {
@@ -376,13 +383,14 @@ unsigned grid_of(int64_t items)
     return (unsigned)items;
 }
 
-// Pass-B schedules (same arithmetic, different traversal):
+// Pass-B schedules (same arithmetic, different traversal or occupancy):
 //   0  micro-tiles 8x2x2, inner b loop rolled
 //   1  micro-tiles 8x2x2, inner b loop unrolled
 //   2  x rows (no micro-tiles), inner b loop rolled
+//   3  x rows, registers capped for 4 CTAs/SM also with the fused action
 // The process-wide choice per precision is set by lqcd_set_force_variant or
 // lqcd_autotune_force; -1 means the default.
-constexpr int kSfVariants = 3;
+constexpr int kSfVariants = 4;
 constexpr int kSfDefault = 2;
 std::atomic<int> g_sf_variant[2] = {{-1}, {-1}};
 
@@ -399,7 +407,7 @@ void set_traversal(SfLattice &L, int variant)
     L.sweep[0] = block_extent(L.dims[0], 64);
     L.sweep[1] = block_extent(L.dims[1], 16);
     L.sweep[2] = block_extent(L.dims[2], 16);
-    if (variant == 2) {
+    if (variant == 2 || variant == 3) {
         L.micro[0] = L.sweep[0];
         L.micro[1] = L.micro[2] = 1;
     } else {
@@ -434,7 +442,7 @@ int resolve_variant(const ForceArgs &a)
 template <typename K> unsigned persistent_grid(K kernel, int slot, int64_t work)
 {
     static std::mutex mu;
-    static int cached[64][8] = {{0}};
+    static int cached[64][16] = {{0}};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return grid_of(work);
     int resident = 0;
@@ -456,6 +464,7 @@ cudaError_t launch_pass_b(const SfLattice &L, const KernelScalars &sc, int varia
 {
     const unsigned grid = grid_of(virtual_blocks((int64_t)L.dims[0] * L.dims[1] * L.dims[2] * L.dims[3]));
     if (variant == 1) force_from_staples<R, ACTION, true><<<grid, kBlock, 0, st>>>(L, sc);
+    else if (variant == 3) force_from_staples<R, ACTION, false, true><<<grid, kBlock, 0, st>>>(L, sc);
     else force_from_staples<R, ACTION, false><<<grid, kBlock, 0, st>>>(L, sc);
     return cudaGetLastError();
 }
@@ -468,6 +477,9 @@ cudaError_t launch_pass_b_batched(const SfBatch &B, const KernelScalars &sc, int
     if (variant == 1) {
         auto k = force_from_staples_batched<R, ACTION, true>;
         k<<<persistent_grid(k, slot, B.total), kBlock, 0, st>>>(B, sc);
+    } else if (variant == 3) {
+        auto k = force_from_staples_batched<R, ACTION, false, true>;
+        k<<<persistent_grid(k, 8 + slot, B.total), kBlock, 0, st>>>(B, sc);
     } else {
         auto k = force_from_staples_batched<R, ACTION, false>;
         k<<<persistent_grid(k, slot, B.total), kBlock, 0, st>>>(B, sc);
