@@ -65,6 +65,75 @@ template <typename R> __device__ __forceinline__ R scalar(const KernelScalars &s
     else return s.d[i];
 }
 
+// Storage of the staple planes: compact (rows 0 and 1, 12 reals, the third
+// row rebuilt on load, as for links) or full (all 18 reals in ceil(18/W)
+// lanes, nothing rebuilt: 1.67x the bytes in FP32, fewer instructions).
+template <typename R, bool FULL> struct Staples {
+    using V4 = typename Vec<R>::type;
+    static constexpr int W = Vec<R>::W;
+    static constexpr int LANES = FULL ? (18 + W - 1) / W : 12 / W;
+
+    static __device__ __forceinline__ Mat<R> load(const R *__restrict__ sf, int64_t V, int plane,
+                                                  int64_t n)
+    {
+        if constexpr (!FULL) {
+            return load_link(sf, V, plane, n);
+        } else {
+            const V4 *p = reinterpret_cast<const V4 *>(sf) + (int64_t)plane * LANES * V + n;
+            R r[LANES * W];
+#pragma unroll
+            for (int q = 0; q < LANES; ++q) {
+                const V4 v = __ldg(p + q * V);
+                if constexpr (W == 4) {
+                    r[4 * q + 0] = v.x;
+                    r[4 * q + 1] = v.y;
+                    r[4 * q + 2] = v.z;
+                    r[4 * q + 3] = v.w;
+                } else {
+                    r[2 * q + 0] = v.x;
+                    r[2 * q + 1] = v.y;
+                }
+            }
+            Mat<R> u;
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    u.re[i][j] = r[2 * (3 * i + j)];
+                    u.im[i][j] = r[2 * (3 * i + j) + 1];
+                }
+            return u;
+        }
+    }
+
+    static __device__ __forceinline__ void store(R *__restrict__ sf, int64_t V, int plane, int64_t n,
+                                                 const Mat<R> &u)
+    {
+        if constexpr (!FULL) {
+            store_link(sf, V, plane, n, u);
+        } else {
+            V4 *p = reinterpret_cast<V4 *>(sf) + (int64_t)plane * LANES * V + n;
+            R r[LANES * W];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    r[2 * (3 * i + j)] = u.re[i][j];
+                    r[2 * (3 * i + j) + 1] = u.im[i][j];
+                }
+#pragma unroll
+            for (int e = 18; e < LANES * W; ++e) r[e] = R(0);
+#pragma unroll
+            for (int q = 0; q < LANES; ++q) {
+                V4 v;
+                if constexpr (W == 4) v = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+                else v = make_double2(r[2 * q], r[2 * q + 1]);
+                p[q * V] = v;
+            }
+        }
+    }
+};
+
 // Traversal order of pass B: the lattice is cut into spatial blocks of
 // bx x by x bz sites that run over all t; blocks one after the other, inside
 // a block t-slice by t-slice, inside a slice micro-tiles of mx x my x mz
@@ -161,7 +230,7 @@ __device__ __forceinline__ int batch_entry(const SfBatch &B, int64_t vb)
 // ---------------------------------------------------------------- pass A
 
 // The 24 staples of the 32 sites of virtual block vb: thread = (site, mu).
-template <typename R>
+template <typename R, bool FULL>
 __device__ __forceinline__ void staples_block(const SfLattice &L, const Geom &g, int64_t vb)
 {
     const R *__restrict__ links = static_cast<const R *>(L.links);
@@ -177,30 +246,33 @@ __device__ __forceinline__ void staples_block(const SfLattice &L, const Geom &g,
         const int64_t vp = disp(g, c, nu, 1), vm = disp(g, c, nu, -1);
         // b = +nu:  U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
         Mat<R> t = mul<N, D>(load_link(links, g.V, nu, xm), load_link(links, g.V, mu, x + vp));
-        store_link(sf, g.V, mu * 6 + 2 * iv, x, mul_top2<N, D>(t, load_link(links, g.V, nu, x)));
+        const Mat<R> up = FULL ? mul<N, D>(t, load_link(links, g.V, nu, x))
+                               : mul_top2<N, D>(t, load_link(links, g.V, nu, x));
+        Staples<R, FULL>::store(sf, g.V, mu * 6 + 2 * iv, x, up);
         // b = -nu:  U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu)
         t = mul<D, D>(load_link(links, g.V, nu, xm + vm), load_link(links, g.V, mu, x + vm));
-        store_link(sf, g.V, mu * 6 + 2 * iv + 1, x,
-                   mul_top2<N, N>(t, load_link(links, g.V, nu, x + vm)));
+        const Mat<R> dn = FULL ? mul<N, N>(t, load_link(links, g.V, nu, x + vm))
+                               : mul_top2<N, N>(t, load_link(links, g.V, nu, x + vm));
+        Staples<R, FULL>::store(sf, g.V, mu * 6 + 2 * iv + 1, x, dn);
     }
 }
 
-template <typename R>
+template <typename R, bool FULL>
 __global__ void __launch_bounds__(kBlock) staple_fields(const __grid_constant__ SfLattice L)
 {
     const Geom g = make_geom(L.dims);
     const int64_t nvb = virtual_blocks(g.V);
-    for (int64_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) staples_block<R>(L, g, vb);
+    for (int64_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) staples_block<R, FULL>(L, g, vb);
 }
 
-template <typename R>
+template <typename R, bool FULL>
 __global__ void __launch_bounds__(kBlock) staple_fields_batched(const __grid_constant__ SfBatch B)
 {
     for (int64_t vb = next_virtual_block(B.counter); vb < B.total;
          vb = next_virtual_block(B.counter)) {
         const int c = batch_entry(B, vb);
         const SfLattice &L = B.e[c];
-        staples_block<R>(L, make_geom(L.dims), vb - L.vb_begin);
+        staples_block<R, FULL>(L, make_geom(L.dims), vb - L.vb_begin);
     }
 }
 
@@ -210,7 +282,7 @@ __global__ void __launch_bounds__(kBlock) staple_fields_batched(const __grid_con
 //   t += B_d [ c_cube sum_{b perp rho, d} S_b(k+d) S^{(d)}_b(k) + c_rect S_d(k+d) A_d^dag ]
 // (the orientation of the shared links fixed at compile time, so that each
 // sign has one small loop body).
-template <bool NEG, bool UNROLLQ, typename R>
+template <bool NEG, bool UNROLLQ, bool FULL, typename R>
 __device__ __forceinline__ void d_terms(Mat<R> &t, const R *__restrict__ links,
                                         const R *__restrict__ sf, const Geom &g, const Coord &c,
                                         int rho, int64_t k, int64_t kp, int id, R c_rt, R c_cb)
@@ -230,12 +302,13 @@ __device__ __forceinline__ void d_terms(Mat<R> &t, const R *__restrict__ links,
         const int ib = q == 0 ? (id == 0 ? 1 : 0) : (id == 2 ? 1 : 2);
         const int nub = (rho + 1 + ib) & 3;
         const int jp = 2 * ((nub - nud - 1) & 3);
-        mul_acc<N, FD>(y, load_link(sf, g.V, base + 2 * ib, kd), load_link(sf, g.V, nud * 6 + jp, site2));
-        mul_acc<N, FD>(y, load_link(sf, g.V, base + 2 * ib + 1, kd),
-                       load_link(sf, g.V, nud * 6 + jp + 1, site2));
+        using SIO = Staples<R, FULL>;
+        mul_acc<N, FD>(y, SIO::load(sf, g.V, base + 2 * ib, kd), SIO::load(sf, g.V, nud * 6 + jp, site2));
+        mul_acc<N, FD>(y, SIO::load(sf, g.V, base + 2 * ib + 1, kd),
+                       SIO::load(sf, g.V, nud * 6 + jp + 1, site2));
     }
     scale(y, c_cb);
-    Mat<R> r3 = load_link(sf, g.V, base + jd, kd);
+    Mat<R> r3 = Staples<R, FULL>::load(sf, g.V, base + jd, kd);
     scale(r3, c_rt);
     if constexpr (!NEG) {
         mul_acc<N, D>(y, r3, load_link(links, g.V, nud, k));  // A_d = U_nud(k)
@@ -248,7 +321,7 @@ __device__ __forceinline__ void d_terms(Mat<R> &t, const R *__restrict__ links,
 
 // Force (and the fused momentum step) on the 128 links of virtual block vb;
 // returns the thread's share of the action (0 for a padding site).
-template <typename R, bool ACTION, bool UNROLLQ>
+template <typename R, bool ACTION, bool UNROLLQ, bool FULL>
 __device__ __forceinline__ double force_block(const SfLattice &L, const KernelScalars &sc,
                                               const Geom &g, const Sweep &sw, int64_t vb)
 {
@@ -273,10 +346,11 @@ __device__ __forceinline__ double force_block(const SfLattice &L, const KernelSc
         set_zero(p2);
 #pragma unroll 1
         for (int jj = 0; jj < 6; ++jj) {
-            const Mat<R> s = load_link(sf, g.V, base + jj, k);
+            using SIO = Staples<R, FULL>;
+            const Mat<R> s = SIO::load(sf, g.V, base + jj, k);
             add_to(pl, s);
-            mul_acc<N, N>(p1, load_link(sf, g.V, base + jj, kp), s);
-            mul_acc<N, N>(p2, s, load_link(sf, g.V, base + jj, km));
+            mul_acc<N, N>(p1, SIO::load(sf, g.V, base + jj, kp), s);
+            mul_acc<N, N>(p2, s, SIO::load(sf, g.V, base + jj, km));
         }
         if constexpr (ACTION) tr_pl = re_trace_mul<N, N>(load_link(links, g.V, rho, k), pl);
         t = pl;
@@ -288,9 +362,11 @@ __device__ __forceinline__ double force_block(const SfLattice &L, const KernelSc
     }
     // cubes and the rectangles along d: positive, then negative d
 #pragma unroll 1
-    for (int id = 0; id < 3; ++id) d_terms<false, UNROLLQ>(t, links, sf, g, c, rho, k, kp, id, c_rt, c_cb);
+    for (int id = 0; id < 3; ++id)
+        d_terms<false, UNROLLQ, FULL>(t, links, sf, g, c, rho, k, kp, id, c_rt, c_cb);
 #pragma unroll 1
-    for (int id = 0; id < 3; ++id) d_terms<true, UNROLLQ>(t, links, sf, g, c, rho, k, kp, id, c_rt, c_cb);
+    for (int id = 0; id < 3; ++id)
+        d_terms<true, UNROLLQ, FULL>(t, links, sf, g, c, rho, k, kp, id, c_rt, c_cb);
 
     const Mat<R> m = mul<N, N>(load_link(links, g.V, rho, k), t);
     R f[8];
@@ -319,7 +395,7 @@ template <typename R, bool ACTION, bool DENSE> constexpr int min_blocks()
     return sizeof(R) == 8 ? 2 : ((ACTION && !DENSE) ? 3 : 4);
 }
 
-template <typename R, bool ACTION, bool UNROLLQ, bool DENSE = false>
+template <typename R, bool ACTION, bool UNROLLQ, bool DENSE = false, bool FULL = false>
 __global__ void __launch_bounds__(kBlock, (min_blocks<R, ACTION, DENSE>()))
     force_from_staples(const __grid_constant__ SfLattice L, const __grid_constant__ KernelScalars sc)
 {
@@ -327,7 +403,7 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<R, ACTION, DENSE>()))
     const Sweep sw = make_sweep(L, g);
     const int64_t nvb = virtual_blocks(g.V);
     for (int64_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
-        const double acc = force_block<R, ACTION, UNROLLQ>(L, sc, g, sw, vb);
+        const double acc = force_block<R, ACTION, UNROLLQ, FULL>(L, sc, g, sw, vb);
         if constexpr (ACTION) {
             const double s = block_sum(acc);
             if (threadIdx.x == 0) L.partials[vb] = s;
@@ -335,7 +411,7 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<R, ACTION, DENSE>()))
     }
 }
 
-template <typename R, bool ACTION, bool UNROLLQ, bool DENSE = false>
+template <typename R, bool ACTION, bool UNROLLQ, bool DENSE = false, bool FULL = false>
 __global__ void __launch_bounds__(kBlock, (min_blocks<R, ACTION, DENSE>()))
     force_from_staples_batched(const __grid_constant__ SfBatch B,
                                const __grid_constant__ KernelScalars sc)
@@ -345,7 +421,8 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<R, ACTION, DENSE>()))
         const int c = batch_entry(B, vb);
         const SfLattice &L = B.e[c];
         const Geom g = make_geom(L.dims);
-        const double acc = force_block<R, ACTION, UNROLLQ>(L, sc, g, make_sweep(L, g), vb - L.vb_begin);
+        const double acc =
+            force_block<R, ACTION, UNROLLQ, FULL>(L, sc, g, make_sweep(L, g), vb - L.vb_begin);
         if constexpr (ACTION) {
             const double s = block_sum(acc);
             if (threadIdx.x == 0) L.partials[vb - L.vb_begin] = s;
@@ -388,10 +465,13 @@ unsigned grid_of(int64_t items)
 //   1  micro-tiles 8x2x2, inner b loop unrolled
 //   2  x rows (no micro-tiles), inner b loop rolled
 //   3  x rows, registers capped for 4 CTAs/SM also with the fused action
+//   4  x rows, staple planes stored full (18 reals, no row rebuilt on load)
 // The process-wide choice per precision is set by lqcd_set_force_variant or
-// lqcd_autotune_force; -1 means the default.
-constexpr int kSfVariants = 4;
-constexpr int kSfDefault = 2;
+// lqcd_autotune_force; -1 means the default: x rows with compact staples in
+// FP32, full staples in FP64 (where the row rebuild costs FP64 issue slots;
+// 114 vs 139 ms at 32^3x64 against 5.5 vs 5.1 ms in FP32).
+constexpr int kSfVariants = 5;
+constexpr int kSfDefault[2] = {2, 4};
 std::atomic<int> g_sf_variant[2] = {{-1}, {-1}};
 
 // Largest divisor of L not above cap.
@@ -407,7 +487,7 @@ void set_traversal(SfLattice &L, int variant)
     L.sweep[0] = block_extent(L.dims[0], 64);
     L.sweep[1] = block_extent(L.dims[1], 16);
     L.sweep[2] = block_extent(L.dims[2], 16);
-    if (variant == 2 || variant == 3) {
+    if (variant == 2 || variant == 3 || variant == 4) {
         L.micro[0] = L.sweep[0];
         L.micro[1] = L.micro[2] = 1;
     } else {
@@ -433,8 +513,9 @@ KernelScalars make_scalars(const ForceArgs &a)
 int resolve_variant(const ForceArgs &a)
 {
     if (a.variant >= 0 && a.variant < kSfVariants) return a.variant;
-    const int v = g_sf_variant[a.precision == LQCD_F64 ? 1 : 0].load();
-    return v < 0 ? kSfDefault : v;
+    const int p = a.precision == LQCD_F64 ? 1 : 0;
+    const int v = g_sf_variant[p].load();
+    return v < 0 ? kSfDefault[p] : v;
 }
 
 // CTAs of a persistent launch: as many as are resident on the device at
@@ -442,7 +523,7 @@ int resolve_variant(const ForceArgs &a)
 template <typename K> unsigned persistent_grid(K kernel, int slot, int64_t work)
 {
     static std::mutex mu;
-    static int cached[64][16] = {{0}};
+    static int cached[64][32] = {{0}};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return grid_of(work);
     int resident = 0;
@@ -465,6 +546,8 @@ cudaError_t launch_pass_b(const SfLattice &L, const KernelScalars &sc, int varia
     const unsigned grid = grid_of(virtual_blocks((int64_t)L.dims[0] * L.dims[1] * L.dims[2] * L.dims[3]));
     if (variant == 1) force_from_staples<R, ACTION, true><<<grid, kBlock, 0, st>>>(L, sc);
     else if (variant == 3) force_from_staples<R, ACTION, false, true><<<grid, kBlock, 0, st>>>(L, sc);
+    else if (variant == 4)
+        force_from_staples<R, ACTION, false, false, true><<<grid, kBlock, 0, st>>>(L, sc);
     else force_from_staples<R, ACTION, false><<<grid, kBlock, 0, st>>>(L, sc);
     return cudaGetLastError();
 }
@@ -480,6 +563,9 @@ cudaError_t launch_pass_b_batched(const SfBatch &B, const KernelScalars &sc, int
     } else if (variant == 3) {
         auto k = force_from_staples_batched<R, ACTION, false, true>;
         k<<<persistent_grid(k, 8 + slot, B.total), kBlock, 0, st>>>(B, sc);
+    } else if (variant == 4) {
+        auto k = force_from_staples_batched<R, ACTION, false, false, true>;
+        k<<<persistent_grid(k, 16 + slot, B.total), kBlock, 0, st>>>(B, sc);
     } else {
         auto k = force_from_staples_batched<R, ACTION, false>;
         k<<<persistent_grid(k, slot, B.total), kBlock, 0, st>>>(B, sc);
@@ -501,7 +587,8 @@ template <typename R> cudaError_t launch_sf_t(const ForceArgs &a, cudaStream_t s
     L.action = a.action;
     const KernelScalars sc = make_scalars(a);
     const int64_t nvb = virtual_blocks((int64_t)a.dims[0] * a.dims[1] * a.dims[2] * a.dims[3]);
-    staple_fields<R><<<grid_of(nvb), kBlock, 0, st>>>(L);
+    if (variant == 4) staple_fields<R, true><<<grid_of(nvb), kBlock, 0, st>>>(L);
+    else staple_fields<R, false><<<grid_of(nvb), kBlock, 0, st>>>(L);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (a.action != nullptr) {
@@ -534,8 +621,13 @@ cudaError_t launch_sf_batched_t(const ForceArgs &a, int n, const SfLattice *item
     const KernelScalars sc = make_scalars(a);
     cudaError_t e = cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    auto ka = staple_fields_batched<R>;
-    ka<<<persistent_grid(ka, 3 + (sizeof(R) == 8 ? 4 : 0), B.total), kBlock, 0, st>>>(B);
+    if (variant == 4) {
+        auto ka = staple_fields_batched<R, true>;
+        ka<<<persistent_grid(ka, 24 + (sizeof(R) == 8 ? 4 : 0), B.total), kBlock, 0, st>>>(B);
+    } else {
+        auto ka = staple_fields_batched<R, false>;
+        ka<<<persistent_grid(ka, 3 + (sizeof(R) == 8 ? 4 : 0), B.total), kBlock, 0, st>>>(B);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (!any_action) return launch_pass_b_batched<R, false>(B, sc, variant, st);
@@ -547,11 +639,13 @@ cudaError_t launch_sf_batched_t(const ForceArgs &a, int n, const SfLattice *item
 
 } // namespace
 
+// Room for 24 planes in the larger (full) of the two storage forms, so that
+// every schedule fits the same workspace.
 size_t staple_field_bytes(const int dims[4], int precision)
 {
     const int64_t V = (int64_t)dims[0] * dims[1] * dims[2] * dims[3];
-    const size_t real = precision == LQCD_F64 ? 8 : 4;
-    return ((size_t)(24 * 12) * (size_t)V * real + 255) & ~(size_t)255;
+    const size_t lanes = precision == LQCD_F64 ? Staples<double, true>::LANES : Staples<float, true>::LANES;
+    return ((size_t)24 * lanes * 16 * (size_t)V + 255) & ~(size_t)255;
 }
 
 int staple_force_partials(const int dims[4])
@@ -576,8 +670,9 @@ int staple_force_variants() { return kSfVariants; }
 
 int staple_force_variant(int precision)
 {
-    const int v = g_sf_variant[precision == LQCD_F64 ? 1 : 0].load();
-    return v < 0 ? kSfDefault : v;
+    const int p = precision == LQCD_F64 ? 1 : 0;
+    const int v = g_sf_variant[p].load();
+    return v < 0 ? kSfDefault[p] : v;
 }
 
 void set_staple_force_variant(int precision, int variant)

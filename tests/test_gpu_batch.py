@@ -33,18 +33,24 @@ def _single_step(bs, c, dt):
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_batched_force_step_equals_single(prec):
+    """Bit-equal to the single-lattice call under every pass-B schedule."""
     bs = hmc.initial_batch(MIXED, prec, sigma=0.4, seed=3)
     n = len(MIXED)
-    ref = [_single_step(bs, c, 0.07) for c in range(n)]
-    force = [lqcd.empty_algebra(bs.params.with_(dims=d)) for d in bs.dims]
-    mom = [p.clone() for p in bs.mom]
-    actions = torch.empty(n, dtype=torch.float64, device="cuda")
-    lqcd.md_force_step_batched(bs.params, bs.dims, bs.links, mom=mom, dt=0.07, force=force,
-                               actions=actions, workspace=bs.workspace)
-    for c in range(n):
-        assert torch.equal(force[c], ref[c][0]), c
-        assert torch.equal(mom[c], ref[c][1]), c
-        assert float(actions[c]) == float(ref[c][2]), c
+    try:
+        for v in range(lqcd.force_variant_count(bs.params)):
+            lqcd.set_force_variant(bs.params, v)
+            ref = [_single_step(bs, c, 0.07) for c in range(n)]
+            force = [lqcd.empty_algebra(bs.params.with_(dims=d)) for d in bs.dims]
+            mom = [p.clone() for p in bs.mom]
+            actions = torch.empty(n, dtype=torch.float64, device="cuda")
+            lqcd.md_force_step_batched(bs.params, bs.dims, bs.links, mom=mom, dt=0.07,
+                                       force=force, actions=actions, workspace=bs.workspace)
+            for c in range(n):
+                assert torch.equal(force[c], ref[c][0]), (v, c)
+                assert torch.equal(mom[c], ref[c][1]), (v, c)
+                assert float(actions[c]) == float(ref[c][2]), (v, c)
+    finally:
+        lqcd.set_force_variant(bs.params, -1)
 
 
 def test_batched_force_matches_oracle():
