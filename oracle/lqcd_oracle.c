@@ -3,7 +3,9 @@
  * molecular-dynamics force and the MD momentum / link updates that use it
  * (D. Li, "The Calculation of Force in Lattice Quantum Chromodynamics",
  * Sec. II, Eqs. 18_3_27_30 ... 18_6_6_13 and the force algorithm that follows
- * Eq. 18_6_6_13).
+ * Eq. 18_6_6_13), and the hopping operator of the Wilson fermion matrix with
+ * its force on the links (Sec. III, Eqs. 18_7_17_4 and 18_1_29_19 ...
+ * 18_7_17_30).
  *
  * TEST INFRASTRUCTURE ONLY.  This file is the independent checker of the CUDA
  * library: only the test-suite, the smoke check and the CPU-baseline leg of
@@ -29,7 +31,11 @@
  * finite differences along all 8 generators, the Wilson-action limit against
  * an independent staple formula, uniform-link configurations against a
  * brute-force single-site sum, the identity of Eq. 18_6_6_13, the exponential
- * against scipy.linalg.expm, and leapfrog energy conservation/reversibility.
+ * against scipy.linalg.expm, and leapfrog energy conservation/reversibility;
+ * for Sec. III: the Clifford algebra of the gamma basis, the free-field
+ * (unit-link) plane-wave spectrum of the hopping operator, its gamma_5
+ * hermiticity, gauge covariance, and finite differences of
+ * 2 Re Y^dag calD X along all 8 generators against the hopping force.
  */
 #include <complex.h>
 #include <math.h>
@@ -572,4 +578,178 @@ void oracle_generator(int a, double *out)
 {
     mat3 t = generator(a);
     memcpy(out, &t, sizeof t);
+}
+
+/* ===================================================== Wilson fermion (Sec. III)
+ *
+ * Spinor fields X[V][4][3] (Dirac index alpha, colour index a; complex).
+ * The paper fixes no representation of the Euclidean gamma matrices; this
+ * oracle takes the chiral basis below (Hermitian, gamma_mu^2 = 1,
+ * {gamma_mu, gamma_nu} = 2 delta_{mu nu}, checked by the tests), with
+ * gamma_1..gamma_4 acting along the directions x, y, z, t. */
+
+typedef struct { cplx s[4][3]; } spinor;
+
+/* gamma_mu for mu = 1..4, and gamma_5 = gamma_1 gamma_2 gamma_3 gamma_4 for
+ * mu = 5 (written out as a product, not as a table). */
+static void gamma_matrix(int mu, cplx g[4][4])
+{
+    memset(g, 0, 16 * sizeof(cplx));
+    switch (mu) {
+    case 1: g[0][3] = I;  g[1][2] = I;  g[2][1] = -I; g[3][0] = -I; break;
+    case 2: g[0][3] = -1; g[1][2] = 1;  g[2][1] = 1;  g[3][0] = -1; break;
+    case 3: g[0][2] = I;  g[1][3] = -I; g[2][0] = -I; g[3][1] = I;  break;
+    case 4: g[0][2] = 1;  g[1][3] = 1;  g[2][0] = 1;  g[3][1] = 1;  break;
+    case 5: {
+        cplx a[4][4], b[4][4], p[4][4];
+        gamma_matrix(1, a);
+        for (int m = 2; m <= 4; ++m) {
+            gamma_matrix(m, b);
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) {
+                    cplx s = 0;
+                    for (int k = 0; k < 4; ++k) s += a[i][k] * b[k][j];
+                    p[i][j] = s;
+                }
+            memcpy(a, p, sizeof p);
+        }
+        memcpy(g, a, sizeof a);
+        break;
+    }
+    }
+}
+
+/* (1 + sign * gamma_mu) acting on the Dirac index of x. */
+static spinor spin_project(int mu, double sign, const spinor *x)
+{
+    cplx g[4][4];
+    gamma_matrix(mu, g);
+    spinor r;
+    for (int al = 0; al < 4; ++al)
+        for (int a = 0; a < 3; ++a) {
+            cplx s = x->s[al][a];
+            for (int be = 0; be < 4; ++be) s += sign * g[al][be] * x->s[be][a];
+            r.s[al][a] = s;
+        }
+    return r;
+}
+
+/* u acting on the colour index of x. */
+static spinor colour_mul(mat3 u, const spinor *x)
+{
+    spinor r;
+    for (int al = 0; al < 4; ++al)
+        for (int a = 0; a < 3; ++a) {
+            cplx s = 0;
+            for (int b = 0; b < 3; ++b) s += u.m[a][b] * x->s[al][b];
+            r.s[al][a] = s;
+        }
+    return r;
+}
+
+static spinor get_spinor(const double *X, long n)
+{
+    spinor r;
+    memcpy(&r, (const cplx *)X + (size_t)n * 12, sizeof r);
+    return r;
+}
+
+/* The hopping part of the Wilson matrix, Eq. 18_7_17_4:
+ *   (calD X)_n = sum_mu (1 - gamma_mu) U_{n,mu} X_{n+mu}
+ *              + (1 + gamma_mu) U_{n,-mu} X_{n-mu},   U_{n,-mu} = U_{n-mu,mu}^dagger.
+ * out[V][4][3]. */
+void oracle_wilson_hopping(const int dims[4], const double *U, const double *X, double *out)
+{
+    field f = {make_geom(dims), (const cplx *)U};
+    for (long n = 0; n < f.g.V; ++n) {
+        spinor acc;
+        memset(&acc, 0, sizeof acc);
+        for (int mu = 1; mu <= 4; ++mu) {
+            spinor xf = get_spinor(X, step(&f.g, n, mu));
+            spinor fw = spin_project(mu, -1.0, &xf);
+            fw = colour_mul(link_dir(&f, n, mu), &fw);
+            spinor xb = get_spinor(X, step(&f.g, n, -mu));
+            spinor bw = spin_project(mu, +1.0, &xb);
+            bw = colour_mul(link_dir(&f, n, -mu), &bw);
+            for (int al = 0; al < 4; ++al)
+                for (int a = 0; a < 3; ++a) acc.s[al][a] += fw.s[al][a] + bw.s[al][a];
+        }
+        memcpy((cplx *)out + (size_t)n * 12, &acc, sizeof acc);
+    }
+}
+
+/* The hopping-term force on link (k, rho) (rho = 1..4), Eqs. 18_1_29_20_1
+ * to 18_7_17_30, literally:
+ *   Z = (1 - gamma_rho) U_{k,rho} X_{k+rho},  B_{ba} = sum_alpha Z_{alpha b} conj(Y_{k, alpha a}),
+ *   W = Y_{k+rho}^dagger (1 + gamma_rho) U_{k,rho}^dagger  (a row over alpha, a),
+ *   C_{ba} = sum_alpha X_{k, alpha b} W_{alpha a},
+ * and the 8 components of the paper's matrix -i (B - C)_TA = sum_i T_i h^i,
+ *   h^i = -( tr(i T_i (B - C)) + c.c. ),
+ * returned scaled: out[i] = coef * h^i.  With X = (D^dag D)^{-1} phi,
+ * Y = D X and D = A - kappa calD, coef = kappa gives the hopping part of
+ * -d/domega^i [phi^dag (D^dag D)^{-1} phi]  (Eqs. 18_6_24_0, 18_1_29_19). */
+static void hopping_force_link(const field *f, const double *X, const double *Y, long k, int rho,
+                               double coef, double out[8])
+{
+    long kp = step(&f->g, k, rho);
+    mat3 u = get_link(f, k, rho);
+    spinor xk = get_spinor(X, k), yk = get_spinor(Y, k);
+    spinor xp = get_spinor(X, kp), yp = get_spinor(Y, kp);
+
+    spinor ux = colour_mul(u, &xp);
+    spinor z = spin_project(rho, -1.0, &ux);
+    mat3 B = zero3();
+    for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a)
+            for (int al = 0; al < 4; ++al) B.m[b][a] += z.s[al][b] * conj(yk.s[al][a]);
+
+    /* W_{alpha a} = sum_{beta, c} conj(Y_{beta c}) (1 + gamma)_{beta alpha} conj(U_{a c}) */
+    cplx g[4][4];
+    gamma_matrix(rho, g);
+    cplx w[4][3];
+    for (int al = 0; al < 4; ++al)
+        for (int a = 0; a < 3; ++a) {
+            cplx s = 0;
+            for (int be = 0; be < 4; ++be) {
+                cplx pg = (be == al ? 1.0 : 0.0) + g[be][al];
+                for (int c = 0; c < 3; ++c) s += conj(yp.s[be][c]) * pg * conj(u.m[a][c]);
+            }
+            w[al][a] = s;
+        }
+    mat3 C = zero3();
+    for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a)
+            for (int al = 0; al < 4; ++al) C.m[b][a] += xk.s[al][b] * w[al][a];
+
+    mat3 m = add(B, scale(-1.0, C));
+    for (int i = 0; i < 8; ++i) {
+        cplx tr = trace(mul(scale(I, generator(i)), m));
+        out[i] = coef * (-(tr + conj(tr)));
+    }
+}
+
+/* The hopping-term force on every link: out[V][4][8]. */
+void oracle_wilson_hopping_force(const int dims[4], const double *U, const double *X,
+                                 const double *Y, double coef, double *out)
+{
+    field f = {make_geom(dims), (const cplx *)U};
+    for (long k = 0; k < f.g.V; ++k)
+        for (int rho = 1; rho <= 4; ++rho)
+            hopping_force_link(&f, X, Y, k, rho, coef, out + ((size_t)k * 4 + rho - 1) * 8);
+}
+
+/* The same on one link (k, rho = 1..4). */
+void oracle_wilson_hopping_force_link(const int dims[4], const double *U, const double *X,
+                                      const double *Y, double coef, long k, int rho, double out[8])
+{
+    field f = {make_geom(dims), (const cplx *)U};
+    hopping_force_link(&f, X, Y, k, rho, coef, out);
+}
+
+/* gamma_mu (mu = 1..5) as a 4x4 complex matrix, for the tests. */
+void oracle_gamma(int mu, double *out)
+{
+    cplx g[4][4];
+    gamma_matrix(mu, g);
+    memcpy(out, g, sizeof g);
 }

@@ -7,7 +7,9 @@ the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 Array conventions (numpy, C order):
   links    complex128 [V, 4, 3, 3]  U_{n,mu}, site n = x + Lx*(y + Ly*(z + Lz*t))
   omega/p/f float64   [V, 4, 8]     algebra components along T_a = lambda_a/2
-Everything follows D. Li, "The Calculation of Force in Lattice QCD", Sec. II.
+  spinors  complex128 [V, 4, 3]     X_{n, alpha a} (Dirac index alpha, colour a)
+Everything follows D. Li, "The Calculation of Force in Lattice QCD", Sec. II
+(gauge action and force) and Sec. III (Wilson hopping operator and its force).
 """
 from __future__ import annotations
 
@@ -67,6 +69,12 @@ def lib():
         L.oracle_algebra_to_matrix.argtypes = [_dbl_p, _dbl_p]
         L.oracle_traceless_antihermitian.argtypes = [_dbl_p, _dbl_p]
         L.oracle_generator.argtypes = [ctypes.c_int, _dbl_p]
+        L.oracle_gamma.argtypes = [ctypes.c_int, _dbl_p]
+        L.oracle_wilson_hopping.argtypes = [_int_p, _dbl_p, _dbl_p, _dbl_p]
+        L.oracle_wilson_hopping_force.argtypes = [_int_p, _dbl_p, _dbl_p, _dbl_p, ctypes.c_double,
+                                                  _dbl_p]
+        L.oracle_wilson_hopping_force_link.argtypes = [
+            _int_p, _dbl_p, _dbl_p, _dbl_p, ctypes.c_double, ctypes.c_long, ctypes.c_int, _dbl_p]
     return _lib
 
 
@@ -248,3 +256,44 @@ def omelyan(dims, U, p, beta: float, c, dt: float, nsteps: int, lam: float = OME
 
 def hamiltonian(dims, U, p, beta: float, c) -> float:
     return kinetic_energy(p) + gauge_action(dims, U, beta, c)
+
+
+# ------------------------------------------------------ Wilson fermion (Sec. III)
+
+def gamma(mu: int) -> np.ndarray:
+    """gamma_mu (mu = 1..4, along x, y, z, t) and gamma_5 (mu = 5) of the
+    oracle's chiral basis, 4x4 complex."""
+    out = np.zeros((4, 4), dtype=np.complex128)
+    lib().oracle_gamma(int(mu), _d(out.view(np.float64)))
+    return out
+
+
+def wilson_hopping(dims, U, X) -> np.ndarray:
+    """calD X of Eq. 18_7_17_4; X, result complex [V, 4, 3]."""
+    U = _cplx(U)
+    X = _cplx(X)
+    out = np.zeros_like(X)
+    lib().oracle_wilson_hopping(_dims(dims), _d(U.view(np.float64)), _d(X.view(np.float64)),
+                                _d(out.view(np.float64)))
+    return out
+
+
+def wilson_hopping_force(dims, U, X, Y, coef: float = 1.0) -> np.ndarray:
+    """coef * h[V, 4, 8], h^i = -(tr(i T_i (B - C)) + c.c.) on every link
+    (Eqs. 18_1_29_20_1 to 18_7_17_30)."""
+    U, X, Y = _cplx(U), _cplx(X), _cplx(Y)
+    out = np.zeros((U.shape[0], 4, 8))
+    lib().oracle_wilson_hopping_force(_dims(dims), _d(U.view(np.float64)),
+                                      _d(X.view(np.float64)), _d(Y.view(np.float64)),
+                                      float(coef), _d(out))
+    return out
+
+
+def wilson_hopping_force_link(dims, U, X, Y, coef: float, site: int, rho: int) -> np.ndarray:
+    """The same on one link; rho = 0..3."""
+    U, X, Y = _cplx(U), _cplx(X), _cplx(Y)
+    out = np.zeros(8)
+    lib().oracle_wilson_hopping_force_link(_dims(dims), _d(U.view(np.float64)),
+                                           _d(X.view(np.float64)), _d(Y.view(np.float64)),
+                                           float(coef), int(site), int(rho) + 1, _d(out))
+    return out

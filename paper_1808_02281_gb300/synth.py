@@ -13,6 +13,8 @@ branch only), so the values are the same on every machine and numpy version.
 
 Draw order for a field of shape [V, 4, 8]: site (x fastest), then direction
 mu = 0..3, then algebra index a = 0..7 -- normal number  (n*4 + mu)*8 + a.
+Spinor fields [V, 4, 3] complex: site, Dirac index, colour, then real and
+imaginary part -- normal number ((n*4 + alpha)*3 + a)*2 + (0 re, 1 im).
 """
 from __future__ import annotations
 
@@ -72,6 +74,13 @@ def gauge_parameters(dims, seed: int, sigma: float = 1.0) -> np.ndarray:
     """Algebra parameters v_a ~ N(0, sigma^2) of a gauge rotation g_n, [V, 8]."""
     V = volume(dims)
     return (sigma * normals(seed, V * 8)).reshape(V, 8)
+
+
+def spinor(dims, seed: int) -> np.ndarray:
+    """Gaussian spinor field, real and imaginary parts ~ N(0, 1):
+    float64 [V, 4, 3, 2] (site, Dirac index, colour, re/im)."""
+    V = volume(dims)
+    return normals(seed, V * 24).reshape(V, 4, 3, 2)
 
 
 def sample_links(n_links: int, count: int, seed: int) -> np.ndarray:
