@@ -275,6 +275,46 @@ LQCD_API int lqcd_convert_algebra(const lqcd_desc *desc, const void *src, int ds
 LQCD_API int lqcd_pack_links(const lqcd_desc *desc, const void *full, void *links, void *stream);
 LQCD_API int lqcd_unpack_links(const lqcd_desc *desc, const void *links, void *full, void *stream);
 
+/* ---------------------------------------------- Wilson fermion (Sec. III)
+ *
+ * Spinor fields hold 4 (Dirac) x 3 (colour) complex numbers per site:
+ * real r = 2*(3*alpha + a) + (0 re, 1 im), r = 0..23, of site n at
+ * ((r/W)*V + n)*W + r%W (W = 4 floats or 2 doubles), i.e. 24*V reals in
+ * 16-byte lanes like the links; device memory, 16-byte aligned.  The paper
+ * fixes no representation of the Euclidean gamma matrices; the library uses
+ * the chiral basis (gamma_mu along x, y, z, t = directions 0..3):
+ *   gamma_x = [[0,0,0,i],[0,0,i,0],[0,-i,0,0],[-i,0,0,0]]
+ *   gamma_y = [[0,0,0,-1],[0,0,1,0],[0,1,0,0],[-1,0,0,0]]
+ *   gamma_z = [[0,0,i,0],[0,0,0,-i],[-i,0,0,0],[0,i,0,0]]
+ *   gamma_t = [[0,0,1,0],[0,0,0,1],[1,0,0,0],[0,1,0,0]]
+ * Only desc->dims and desc->precision are read by these calls.
+ *
+ * lqcd_wilson_dslash: y = a x + b calD x with the hopping operator of
+ * Eq. 18_7_17_4,
+ *   (calD x)_n = sum_mu (1 - gamma_mu) U_{n,mu} x_{n+mu}
+ *              + (1 + gamma_mu) U_{n-mu,mu}^dagger x_{n-mu}  (periodic).
+ * a = 1, b = -kappa gives Y = D X of Eq. 18_7_17_2 without the clover term.
+ * x (read) and y (written) must not overlap; a, b finite. */
+LQCD_API int lqcd_wilson_dslash(const lqcd_desc *desc, const void *links, const void *x, double a,
+                                double b, void *y, void *stream);
+
+/* lqcd_wilson_hopping_force: the hopping-term force of Eqs. 18_1_29_19 to
+ * 18_7_17_30 on every link (k, rho):
+ *   B = ((1 - gamma_rho) U_{k,rho} X_{k+rho}) (x) Y_k^dagger,
+ *   C = X_k (x) (Y_{k+rho}^dagger (1 + gamma_rho) U_{k,rho}^dagger)
+ * (outer products in colour, summed over the Dirac index), and the
+ * components h^i of the Hermitian matrix -i (B - C)_TA = sum_i T_i h^i,
+ * h^i = -(tr(i T_i (B - C)) + c.c.).  The result is f = coef * h: with
+ * X = (D^dagger D)^{-1} phi, Y = D X and D = A - kappa calD, coef = kappa
+ * gives the hopping part of -d/domega [phi^dagger (D^dagger D)^{-1} phi]
+ * (Eq. 18_6_24_0), the term to add to the gauge force.
+ * X, Y: spinor layout (read).  force: algebra layout, written if not NULL;
+ * mom: algebra layout, mom += dt * f if not NULL (at least one of the two).
+ * coef, dt finite.  The outputs must not overlap the inputs. */
+LQCD_API int lqcd_wilson_hopping_force(const lqcd_desc *desc, const void *links, const void *X,
+                                       const void *Y, double coef, void *force, void *mom,
+                                       double dt, void *stream);
+
 /* Bytes of device workspace that this descriptor needs on the current
  * device: the staple planes and action partials of the staple-field force
  * (force_algo STAPLE_FIELDS or AUTO; 24 SU(3) planes per site -- 1920 bytes

@@ -658,24 +658,39 @@ static spinor get_spinor(const double *X, long n)
  *   (calD X)_n = sum_mu (1 - gamma_mu) U_{n,mu} X_{n+mu}
  *              + (1 + gamma_mu) U_{n,-mu} X_{n-mu},   U_{n,-mu} = U_{n-mu,mu}^dagger.
  * out[V][4][3]. */
+static spinor hopping_site(const field *f, const double *X, long n)
+{
+    spinor acc;
+    memset(&acc, 0, sizeof acc);
+    for (int mu = 1; mu <= 4; ++mu) {
+        spinor xf = get_spinor(X, step(&f->g, n, mu));
+        spinor fw = spin_project(mu, -1.0, &xf);
+        fw = colour_mul(link_dir(f, n, mu), &fw);
+        spinor xb = get_spinor(X, step(&f->g, n, -mu));
+        spinor bw = spin_project(mu, +1.0, &xb);
+        bw = colour_mul(link_dir(f, n, -mu), &bw);
+        for (int al = 0; al < 4; ++al)
+            for (int a = 0; a < 3; ++a) acc.s[al][a] += fw.s[al][a] + bw.s[al][a];
+    }
+    return acc;
+}
+
 void oracle_wilson_hopping(const int dims[4], const double *U, const double *X, double *out)
 {
     field f = {make_geom(dims), (const cplx *)U};
     for (long n = 0; n < f.g.V; ++n) {
-        spinor acc;
-        memset(&acc, 0, sizeof acc);
-        for (int mu = 1; mu <= 4; ++mu) {
-            spinor xf = get_spinor(X, step(&f.g, n, mu));
-            spinor fw = spin_project(mu, -1.0, &xf);
-            fw = colour_mul(link_dir(&f, n, mu), &fw);
-            spinor xb = get_spinor(X, step(&f.g, n, -mu));
-            spinor bw = spin_project(mu, +1.0, &xb);
-            bw = colour_mul(link_dir(&f, n, -mu), &bw);
-            for (int al = 0; al < 4; ++al)
-                for (int a = 0; a < 3; ++a) acc.s[al][a] += fw.s[al][a] + bw.s[al][a];
-        }
+        spinor acc = hopping_site(&f, X, n);
         memcpy((cplx *)out + (size_t)n * 12, &acc, sizeof acc);
     }
+}
+
+/* (calD X)_n at the single site n: out[4][3]. */
+void oracle_wilson_hopping_site(const int dims[4], const double *U, const double *X, long n,
+                                double *out)
+{
+    field f = {make_geom(dims), (const cplx *)U};
+    spinor acc = hopping_site(&f, X, n);
+    memcpy(out, &acc, sizeof acc);
 }
 
 /* The hopping-term force on link (k, rho) (rho = 1..4), Eqs. 18_1_29_20_1

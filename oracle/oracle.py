@@ -71,6 +71,7 @@ def lib():
         L.oracle_generator.argtypes = [ctypes.c_int, _dbl_p]
         L.oracle_gamma.argtypes = [ctypes.c_int, _dbl_p]
         L.oracle_wilson_hopping.argtypes = [_int_p, _dbl_p, _dbl_p, _dbl_p]
+        L.oracle_wilson_hopping_site.argtypes = [_int_p, _dbl_p, _dbl_p, ctypes.c_long, _dbl_p]
         L.oracle_wilson_hopping_force.argtypes = [_int_p, _dbl_p, _dbl_p, _dbl_p, ctypes.c_double,
                                                   _dbl_p]
         L.oracle_wilson_hopping_force_link.argtypes = [
@@ -275,6 +276,15 @@ def wilson_hopping(dims, U, X) -> np.ndarray:
     out = np.zeros_like(X)
     lib().oracle_wilson_hopping(_dims(dims), _d(U.view(np.float64)), _d(X.view(np.float64)),
                                 _d(out.view(np.float64)))
+    return out
+
+
+def wilson_hopping_site(dims, U, X, site: int) -> np.ndarray:
+    """(calD X)_site, complex [4, 3]."""
+    U, X = _cplx(U), _cplx(X)
+    out = np.zeros((4, 3), dtype=np.complex128)
+    lib().oracle_wilson_hopping_site(_dims(dims), _d(U.view(np.float64)), _d(X.view(np.float64)),
+                                     int(site), _d(out.view(np.float64)))
     return out
 
 

@@ -473,6 +473,50 @@ int lqcd_omega_gradient(const lqcd_desc *desc, const void *omega, const void *fo
     return cuda_status(lqcd::launch_omega_gradient(a, as_stream(stream)));
 }
 
+int lqcd_wilson_dslash(const lqcd_desc *desc, const void *links, const void *x, double a, double b,
+                       void *y, void *stream)
+{
+    int s = check_desc(desc);
+    if (s) return s;
+    if ((s = check_ptrs({links, x, y}))) return s;
+    if (x == y || y == links || !std::isfinite(a) || !std::isfinite(b)) return LQCD_ERR_ARG;
+    lqcd::WilsonArgs w{};
+    copy_dims(w.dims, desc);
+    w.precision = desc->precision;
+    w.links = links;
+    w.x = x;
+    w.out = y;
+    w.ca = a;
+    w.cb = b;
+    return cuda_status(lqcd::launch_wilson_dslash(w, as_stream(stream)));
+}
+
+int lqcd_wilson_hopping_force(const lqcd_desc *desc, const void *links, const void *X, const void *Y,
+                              double coef, void *force, void *mom, double dt, void *stream)
+{
+    int s = check_desc(desc);
+    if (s) return s;
+    if ((s = check_ptrs({links, X, Y}))) return s;
+    if (force == nullptr && mom == nullptr) return LQCD_ERR_ARG;
+    if (force != nullptr && (s = check_ptrs({force}))) return s;
+    if (mom != nullptr && (s = check_ptrs({mom}))) return s;
+    if (force != nullptr && force == mom) return LQCD_ERR_ARG;
+    for (const void *o : {(const void *)force, (const void *)mom})
+        if (o != nullptr && (o == links || o == X || o == Y)) return LQCD_ERR_ARG;
+    if (!std::isfinite(coef) || !std::isfinite(dt)) return LQCD_ERR_ARG;
+    lqcd::WilsonArgs w{};
+    copy_dims(w.dims, desc);
+    w.precision = desc->precision;
+    w.links = links;
+    w.x = X;
+    w.y = Y;
+    w.force = force;
+    w.mom = mom;
+    w.coef = coef;
+    w.dt = dt;
+    return cuda_status(lqcd::launch_wilson_hopping_force(w, as_stream(stream)));
+}
+
 static int convert_common(const lqcd_desc *desc, const void *src, int dst_precision, void *dst,
                           bool links, void *stream)
 {

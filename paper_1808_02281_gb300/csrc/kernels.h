@@ -153,4 +153,21 @@ cudaError_t launch_convert(const MdArgs &a, int dst_precision, bool links, cudaS
 cudaError_t launch_pack(const MdArgs &a, cudaStream_t st);
 cudaError_t launch_unpack(const MdArgs &a, cudaStream_t st);
 
+// Wilson fermion hopping term (Sec. III).  Spinor fields: 24 reals per site,
+// real r = 2*(3*alpha + a) + (0 re, 1 im) of site n at ((r/W)*V + n)*W + r%W.
+struct WilsonArgs {
+    int dims[4];
+    int precision;
+    const void *links;
+    const void *x;   // dslash input; force: X
+    const void *y;   // force: Y
+    void *out;       // dslash output
+    void *force;     // force output (or null)
+    void *mom;       // momenta updated in place (or null)
+    double ca, cb;   // dslash: out = ca * x + cb * calD x
+    double coef, dt; // force: f = coef * h;  mom += dt * f
+};
+cudaError_t launch_wilson_dslash(const WilsonArgs &a, cudaStream_t st);
+cudaError_t launch_wilson_hopping_force(const WilsonArgs &a, cudaStream_t st);
+
 } // namespace lqcd

@@ -1,0 +1,354 @@
+// Wilson fermion hopping term (Sec. III of the paper): the hopping operator
+// calD of Eq. 18_7_17_4 applied to a spinor field, and the hopping-term force
+// on every link, -i(B - C)_TA of Eqs. 18_1_29_19 to 18_7_17_30.
+//
+// Both are HBM-streaming kernels (a few hundred flops per 100-400 bytes), so
+// the design is about bytes: spinors and links are read in 16-byte lanes,
+// neighbours come from L1/L2 (a time slice of a 32^3 spinor field is 3 MB),
+// and every (1 -+ gamma_mu) is applied as a spin projection to two colour
+// vectors, so that each link multiplies two colour vectors instead of four.
+#include "kernels.h"
+#include "su3.cuh"
+
+namespace lqcd {
+namespace {
+
+// ------------------------------------------------------------ gamma basis
+
+// Euclidean gamma matrices of the chiral basis, gamma_mu acting along
+// direction mu = x, y, z, t.  Each has one non-zero entry per row:
+// gamma_mu[alpha][gperm(mu, alpha)] = i^gcode(mu, alpha):
+//   gamma_x: columns 3 2 1 0, entries  i  i -i -i
+//   gamma_y: columns 3 2 1 0, entries -1  1  1 -1
+//   gamma_z: columns 2 3 0 1, entries  i -i -i  i
+//   gamma_t: columns 2 3 0 1, entries  1  1  1  1
+__host__ __device__ constexpr int gperm(int mu, int alpha) { return mu < 2 ? 3 - alpha : alpha ^ 2; }
+
+__host__ __device__ constexpr int gcode(int mu, int alpha)
+{
+    return mu == 0   ? (alpha < 2 ? 1 : 3)
+           : mu == 1 ? ((alpha == 0 || alpha == 3) ? 2 : 0)
+           : mu == 2 ? ((alpha == 0 || alpha == 3) ? 1 : 3)
+                     : 0;
+}
+
+// (re, im) = i^K (xr + i xi)
+template <int K, typename R> __device__ __forceinline__ void times_ipow(R &re, R &im, R xr, R xi)
+{
+    constexpr int k = K & 3;
+    if constexpr (k == 0) {
+        re = xr;
+        im = xi;
+    } else if constexpr (k == 1) {
+        re = -xi;
+        im = xr;
+    } else if constexpr (k == 2) {
+        re = -xr;
+        im = -xi;
+    } else {
+        re = xi;
+        im = -xr;
+    }
+}
+
+template <typename R> struct Spinor {
+    R re[4][3], im[4][3];
+};
+// Two colour vectors: the independent rows 0 and 1 of (1 + s gamma_mu) psi.
+template <typename R> struct Half {
+    R re[2][3], im[2][3];
+};
+
+// ------------------------------------------------------------ spinor I/O
+
+template <typename R>
+__device__ __forceinline__ Spinor<R> load_spinor(const R *__restrict__ x, int64_t V, int64_t n)
+{
+    using V4 = typename Vec<R>::type;
+    constexpr int W = Vec<R>::W;
+    const V4 *p = reinterpret_cast<const V4 *>(x) + n;
+    R r[24];
+#pragma unroll
+    for (int q = 0; q < 24 / W; ++q) {
+        const V4 v = __ldg(p + q * V);
+        if constexpr (W == 4) {
+            r[4 * q + 0] = v.x;
+            r[4 * q + 1] = v.y;
+            r[4 * q + 2] = v.z;
+            r[4 * q + 3] = v.w;
+        } else {
+            r[2 * q + 0] = v.x;
+            r[2 * q + 1] = v.y;
+        }
+    }
+    Spinor<R> s;
+#pragma unroll
+    for (int al = 0; al < 4; ++al)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            s.re[al][a] = r[2 * (3 * al + a)];
+            s.im[al][a] = r[2 * (3 * al + a) + 1];
+        }
+    return s;
+}
+
+template <typename R>
+__device__ __forceinline__ void store_spinor(R *__restrict__ x, int64_t V, int64_t n, const Spinor<R> &s)
+{
+    using V4 = typename Vec<R>::type;
+    constexpr int W = Vec<R>::W;
+    V4 *p = reinterpret_cast<V4 *>(x) + n;
+    R r[24];
+#pragma unroll
+    for (int al = 0; al < 4; ++al)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            r[2 * (3 * al + a)] = s.re[al][a];
+            r[2 * (3 * al + a) + 1] = s.im[al][a];
+        }
+#pragma unroll
+    for (int q = 0; q < 24 / W; ++q) {
+        V4 v;
+        if constexpr (W == 4) v = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+        else v = make_double2(r[2 * q], r[2 * q + 1]);
+        p[q * V] = v;
+    }
+}
+
+// ------------------------------------------------ spin projection algebra
+
+// Rows 0 and 1 of (1 + S gamma_MU) x.  Rows gperm(MU, 0) and gperm(MU, 1) of
+// the same spinor are S i^gcode(MU, gperm) times them (gamma_MU^2 = 1), so
+// these two colour vectors carry all of it.
+template <int MU, int S, int AL, typename R>
+__device__ __forceinline__ void project_row(Half<R> &h, const Spinor<R> &x)
+{
+    constexpr int p = gperm(MU, AL);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        R tr, ti;
+        times_ipow<gcode(MU, AL) + (S < 0 ? 2 : 0)>(tr, ti, x.re[p][a], x.im[p][a]);
+        h.re[AL][a] = x.re[AL][a] + tr;
+        h.im[AL][a] = x.im[AL][a] + ti;
+    }
+}
+
+template <int MU, int S, typename R> __device__ __forceinline__ Half<R> project(const Spinor<R> &x)
+{
+    Half<R> h;
+    project_row<MU, S, 0>(h, x);
+    project_row<MU, S, 1>(h, x);
+    return h;
+}
+
+// acc += (1 + S gamma_MU) applied form of the half spinor g: rows 0, 1 are g,
+// row gperm(MU, alpha) is S i^gcode(MU, gperm(MU, alpha)) g_alpha.
+template <int MU, int S, typename R>
+__device__ __forceinline__ void accumulate(Spinor<R> &acc, const Half<R> &g)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        R tr, ti;
+        acc.re[0][a] += g.re[0][a];
+        acc.im[0][a] += g.im[0][a];
+        acc.re[1][a] += g.re[1][a];
+        acc.im[1][a] += g.im[1][a];
+        constexpr int p0 = gperm(MU, 0), p1 = gperm(MU, 1);
+        times_ipow<gcode(MU, p0) + (S < 0 ? 2 : 0)>(tr, ti, g.re[0][a], g.im[0][a]);
+        acc.re[p0][a] += tr;
+        acc.im[p0][a] += ti;
+        times_ipow<gcode(MU, p1) + (S < 0 ? 2 : 0)>(tr, ti, g.re[1][a], g.im[1][a]);
+        acc.re[p1][a] += tr;
+        acc.im[p1][a] += ti;
+    }
+}
+
+// op(u) applied to both colour vectors of h (F = N: u, F = D: u^dagger).
+template <int F, typename R> __device__ __forceinline__ Half<R> colour_mul(const Mat<R> &u, const Half<R> &h)
+{
+    Half<R> r;
+#pragma unroll
+    for (int al = 0; al < 2; ++al)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            R re = R(0), im = R(0);
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                re = fma(el_re<F>(u, a, b), h.re[al][b], re);
+                re = fma(-el_im<F>(u, a, b), h.im[al][b], re);
+                im = fma(el_re<F>(u, a, b), h.im[al][b], im);
+                im = fma(el_im<F>(u, a, b), h.re[al][b], im);
+            }
+            r.re[al][a] = re;
+            r.im[al][a] = im;
+        }
+    return r;
+}
+
+// m[b][a] += SIGN * sum_alpha p_alpha[b] conj(q_alpha[a]) over the two rows.
+template <int SIGN, typename R>
+__device__ __forceinline__ void outer_acc(Mat<R> &m, const Half<R> &p, const Half<R> &q)
+{
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            R re = m.re[b][a], im = m.im[b][a];
+#pragma unroll
+            for (int al = 0; al < 2; ++al) {
+                // p * conj(q) = (pr qr + pi qi) + i (pi qr - pr qi)
+                re = fma(R(SIGN) * p.re[al][b], q.re[al][a], re);
+                re = fma(R(SIGN) * p.im[al][b], q.im[al][a], re);
+                im = fma(R(SIGN) * p.im[al][b], q.re[al][a], im);
+                im = fma(-R(SIGN) * p.re[al][b], q.im[al][a], im);
+            }
+            m.re[b][a] = re;
+            m.im[b][a] = im;
+        }
+}
+
+// ------------------------------------------------------- hopping operator
+
+// acc += (1 - gamma_MU) U_{n,MU} x_{n+MU} + (1 + gamma_MU) U_{n-MU,MU}^dag x_{n-MU}
+template <int MU, typename R>
+__device__ __forceinline__ void hop(Spinor<R> &acc, const R *__restrict__ links,
+                                    const R *__restrict__ x, const Geom &g, const Coord &c, int64_t n)
+{
+    const int64_t nf = n + disp(g, c, MU, 1);
+    accumulate<MU, -1>(acc, colour_mul<N>(load_link(links, g.V, MU, n), project<MU, -1>(load_spinor(x, g.V, nf))));
+    const int64_t nb = n + disp(g, c, MU, -1);
+    accumulate<MU, +1>(acc, colour_mul<D>(load_link(links, g.V, MU, nb), project<MU, +1>(load_spinor(x, g.V, nb))));
+}
+
+constexpr int kDslashBlock = 128;
+
+// out_n = ca x_n + cb (calD x)_n, one thread per site.
+template <typename R>
+__global__ void __launch_bounds__(kDslashBlock) wilson_dslash(const __grid_constant__ WilsonArgs a)
+{
+    const Geom g = make_geom(a.dims);
+    const R *__restrict__ links = static_cast<const R *>(a.links);
+    const R *__restrict__ x = static_cast<const R *>(a.x);
+    R *__restrict__ out = static_cast<R *>(a.out);
+    const R ca = R(a.ca), cb = R(a.cb);
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < g.V;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        const Coord c = coord_of(g, n);
+        Spinor<R> acc;
+#pragma unroll
+        for (int al = 0; al < 4; ++al)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) acc.re[al][b] = acc.im[al][b] = R(0);
+        hop<0>(acc, links, x, g, c, n);
+        hop<1>(acc, links, x, g, c, n);
+        hop<2>(acc, links, x, g, c, n);
+        hop<3>(acc, links, x, g, c, n);
+        if (a.ca != 0.0) {
+            const Spinor<R> xn = load_spinor(x, g.V, n);
+#pragma unroll
+            for (int al = 0; al < 4; ++al)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    acc.re[al][b] = fma(ca, xn.re[al][b], cb * acc.re[al][b]);
+                    acc.im[al][b] = fma(ca, xn.im[al][b], cb * acc.im[al][b]);
+                }
+        } else {
+#pragma unroll
+            for (int al = 0; al < 4; ++al)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    acc.re[al][b] *= cb;
+                    acc.im[al][b] *= cb;
+                }
+        }
+        store_spinor(out, g.V, n, acc);
+    }
+}
+
+// --------------------------------------------------- hopping-term force
+
+// B - C on link (k, RHO), both as sums over the two independent spin rows:
+//   B = sum_alpha (U chi_alpha) (x) psi_alpha^dag,  chi = (1 - g) X_{k+rho}, psi = (1 - g) Y_k
+//   C = sum_alpha xi_alpha (x) (U eta_alpha)^dag,   xi = (1 + g) X_k,      eta = (1 + g) Y_{k+rho}
+// (Eqs. 18_1_29_20_2 and 18_1_29_20_3 with (1 -+ g) Hermitian and
+// (1 -+ g)^2 = 2 (1 -+ g), so the projector moves onto the other factor and
+// the four spin rows fold into two.)
+template <int RHO, typename R>
+__device__ __forceinline__ Mat<R> b_minus_c(const R *__restrict__ links, const R *__restrict__ X,
+                                            const R *__restrict__ Y, int64_t V, int64_t k, int64_t kp)
+{
+    const Mat<R> u = load_link(links, V, RHO, k);
+    Mat<R> m;
+    set_zero(m);
+    outer_acc<1>(m, colour_mul<N>(u, project<RHO, -1>(load_spinor(X, V, kp))),
+                 project<RHO, -1>(load_spinor(Y, V, k)));
+    outer_acc<-1>(m, project<RHO, +1>(load_spinor(X, V, k)),
+                  colour_mul<N>(u, project<RHO, +1>(load_spinor(Y, V, kp))));
+    return m;
+}
+
+constexpr int kForceBlock = 128; // 32 sites x 4 directions, one direction per warp
+
+template <typename R>
+__global__ void __launch_bounds__(kForceBlock) wilson_hopping_force(const __grid_constant__ WilsonArgs a)
+{
+    const Geom g = make_geom(a.dims);
+    const R *__restrict__ links = static_cast<const R *>(a.links);
+    const R *__restrict__ X = static_cast<const R *>(a.x);
+    const R *__restrict__ Y = static_cast<const R *>(a.y);
+    const int rho = (int)(threadIdx.x >> 5);
+    const int64_t k = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
+    if (k >= g.V) return;
+    const Coord c = coord_of(g, k);
+    const int64_t kp = k + disp(g, c, rho, 1);
+    Mat<R> m;
+    switch (rho) {
+    case 0: m = b_minus_c<0>(links, X, Y, g.V, k, kp); break;
+    case 1: m = b_minus_c<1>(links, X, Y, g.V, k, kp); break;
+    case 2: m = b_minus_c<2>(links, X, Y, g.V, k, kp); break;
+    default: m = b_minus_c<3>(links, X, Y, g.V, k, kp); break;
+    }
+    // f^i = coef * h^i,  h^i = -(tr(i T_i M) + c.c.) = Im tr(lambda_i M)
+    R f[8];
+    ta_components(m, R(-a.coef), f);
+    if (a.force != nullptr) store_algebra(static_cast<R *>(a.force), g.V, rho, k, f);
+    if (a.mom != nullptr) {
+        R *mom = static_cast<R *>(a.mom);
+        R p[8];
+        load_algebra(mom, g.V, rho, k, p);
+        const R dt = R(a.dt);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) p[q] = fma(dt, f[q], p[q]);
+        store_algebra(mom, g.V, rho, k, p);
+    }
+}
+
+unsigned blocks_for(int64_t items, int per_block)
+{
+    int64_t b = (items + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > ((int64_t)1 << 30)) b = (int64_t)1 << 30;
+    return (unsigned)b;
+}
+
+} // namespace
+
+cudaError_t launch_wilson_dslash(const WilsonArgs &a, cudaStream_t st)
+{
+    const int64_t V = (int64_t)a.dims[0] * a.dims[1] * a.dims[2] * a.dims[3];
+    const unsigned grid = blocks_for(V, kDslashBlock);
+    if (a.precision == LQCD_F64) wilson_dslash<double><<<grid, kDslashBlock, 0, st>>>(a);
+    else wilson_dslash<float><<<grid, kDslashBlock, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wilson_hopping_force(const WilsonArgs &a, cudaStream_t st)
+{
+    const int64_t V = (int64_t)a.dims[0] * a.dims[1] * a.dims[2] * a.dims[3];
+    const unsigned grid = blocks_for(V, 32);
+    if (a.precision == LQCD_F64) wilson_hopping_force<double><<<grid, kForceBlock, 0, st>>>(a);
+    else wilson_hopping_force<float><<<grid, kForceBlock, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+} // namespace lqcd

@@ -81,6 +81,12 @@ _EXPORTS = {
                                             ctypes.c_void_p]),
     "lqcd_pack_links": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "lqcd_unpack_links": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "lqcd_wilson_dslash": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                                          ctypes.c_void_p]),
+    "lqcd_wilson_hopping_force": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
+                                                 ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]),
     "lqcd_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(Desc)]),
     "lqcd_workspace_bytes_batched": (ctypes.c_size_t, [ctypes.POINTER(Desc), ctypes.c_int,
                                                        ctypes.POINTER(LatticeRef)]),
@@ -169,6 +175,10 @@ class Lattice:
     def algebra_shape(self):
         return (4, 8 // self.W, self.V, self.W)
 
+    @property
+    def spinor_shape(self):
+        return (24 // self.W, self.V, self.W)
+
     def desc(self) -> Desc:
         d = Desc()
         for i in range(4):
@@ -213,6 +223,45 @@ def empty_links(lat: Lattice, device=None) -> torch.Tensor:
 
 def empty_algebra(lat: Lattice, device=None) -> torch.Tensor:
     return torch.empty(lat.algebra_shape, dtype=lat.dtype, device=device or "cuda")
+
+
+def empty_spinor(lat: Lattice, device=None) -> torch.Tensor:
+    return torch.empty(lat.spinor_shape, dtype=lat.dtype, device=device or "cuda")
+
+
+def wilson_dslash(lat: Lattice, links: torch.Tensor, x: torch.Tensor, a: float = 0.0,
+                  b: float = 1.0, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """y = a x + b calD x, calD the Wilson hopping operator (Eq. 18_7_17_4);
+    a = 1, b = -kappa gives D x without the clover term."""
+    _check(links, lat, lat.link_shape, "links")
+    _check(x, lat, lat.spinor_shape, "x")
+    out = empty_spinor(lat, x.device) if out is None else out
+    _check(out, lat, lat.spinor_shape, "y")
+    d = lat.desc()
+    _call("lqcd_wilson_dslash", ctypes.byref(d), _ptr(links), _ptr(x), float(a), float(b),
+          _ptr(out), _stream(stream))
+    return out
+
+
+def wilson_hopping_force(lat: Lattice, links: torch.Tensor, X: torch.Tensor, Y: torch.Tensor,
+                         coef: float = 1.0, force: torch.Tensor | None = None,
+                         mom: torch.Tensor | None = None, dt: float = 0.0, stream=None):
+    """f = coef * h, h the components of -i(B - C)_TA (Eqs. 18_1_29_19 to
+    18_7_17_30) on every link; stores f into ``force`` and/or applies
+    mom += dt f.  With neither given, returns a new force tensor."""
+    _check(links, lat, lat.link_shape, "links")
+    _check(X, lat, lat.spinor_shape, "X")
+    _check(Y, lat, lat.spinor_shape, "Y")
+    if force is None and mom is None:
+        force = empty_algebra(lat, links.device)
+    for t, name in ((force, "force"), (mom, "mom")):
+        if t is not None:
+            _check(t, lat, lat.algebra_shape, name)
+    d = lat.desc()
+    _call("lqcd_wilson_hopping_force", ctypes.byref(d), _ptr(links), _ptr(X), _ptr(Y),
+          float(coef), None if force is None else _ptr(force),
+          None if mom is None else _ptr(mom), float(dt), _stream(stream))
+    return force
 
 
 def workspace_bytes(lat: Lattice) -> int:
@@ -502,6 +551,28 @@ def algebra_from_device(t: torch.Tensor) -> np.ndarray:
     a = t.detach().to("cpu", torch.float64).numpy()   # [4, 8/W, V, W]
     V = a.shape[2]
     return np.ascontiguousarray(a.transpose(2, 0, 1, 3).reshape(V, 4, 8))
+
+
+def spinor_to_device(lat: Lattice, x: np.ndarray, device="cuda", pin: bool = False) -> torch.Tensor:
+    """Spinor field, complex [V, 4, 3] or float [V, 4, 3, 2] (re, im) numpy
+    -> spinor layout tensor [24/W, V, W] (pure reshape)."""
+    x = np.asarray(x)
+    if np.iscomplexobj(x):
+        x = np.stack([x.real, x.imag], axis=-1)
+    W = lat.W
+    soa = np.ascontiguousarray(x.reshape(lat.V, 24 // W, W).transpose(1, 0, 2))
+    t = torch.from_numpy(soa).to(lat.dtype)
+    if pin:
+        t = t.pin_memory()
+    return t.to(device, non_blocking=pin)
+
+
+def spinor_from_device(t: torch.Tensor) -> np.ndarray:
+    """Spinor layout tensor -> complex128 numpy [V, 4, 3]."""
+    a = t.detach().to("cpu", torch.float64).numpy()   # [24/W, V, W]
+    V = a.shape[1]
+    r = np.ascontiguousarray(a.transpose(1, 0, 2).reshape(V, 4, 3, 2))
+    return r[..., 0] + 1j * r[..., 1]
 
 
 def full_to_device(lat: Lattice, U: np.ndarray, device="cuda") -> torch.Tensor:

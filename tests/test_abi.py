@@ -106,6 +106,47 @@ def test_pointer_checks(lib):
     assert lib.lqcd_kinetic_energy(ctypes.byref(d), MISALIGNED, GOOD2, GOOD, 4096, None) == -3
 
 
+def test_wilson_argument_checks(lib):
+    d = _desc()
+    D = ctypes.c_double
+    GOOD3 = ctypes.c_void_p(0x30000)
+    GOOD4 = ctypes.c_void_p(0x40000)
+    dslash = lib.lqcd_wilson_dslash
+    assert dslash(None, GOOD, GOOD2, D(1), D(-0.1), GOOD3, None) == -1
+    assert dslash(ctypes.byref(d), None, GOOD2, D(1), D(-0.1), GOOD3, None) == -1
+    assert dslash(ctypes.byref(d), GOOD, MISALIGNED, D(1), D(-0.1), GOOD3, None) == -3
+    assert dslash(ctypes.byref(d), GOOD, GOOD2, D(1), D(-0.1), GOOD2, None) == -1    # y == x
+    assert dslash(ctypes.byref(d), GOOD, GOOD2, D(float("nan")), D(-0.1), GOOD3, None) == -1
+    assert dslash(ctypes.byref(_desc(dims=(4, 0, 4, 4))), GOOD, GOOD2, D(1), D(1), GOOD3,
+                  None) == -2
+    force = lib.lqcd_wilson_hopping_force
+    assert force(ctypes.byref(d), GOOD, GOOD2, GOOD3, D(0.1), None, None, D(0), None) == -1
+    assert force(ctypes.byref(d), GOOD, GOOD2, None, D(0.1), GOOD4, None, D(0), None) == -1
+    assert force(ctypes.byref(d), GOOD, GOOD2, GOOD3, D(0.1), MISALIGNED, None, D(0), None) == -3
+    assert force(ctypes.byref(d), GOOD, GOOD2, GOOD3, D(0.1), None, MISALIGNED, D(0), None) == -3
+    assert force(ctypes.byref(d), GOOD, GOOD2, GOOD3, D(0.1), GOOD4, GOOD4, D(0), None) == -1
+    assert force(ctypes.byref(d), GOOD, GOOD2, GOOD3, D(0.1), GOOD2, None, D(0), None) == -1
+    assert force(ctypes.byref(d), GOOD, GOOD2, GOOD3, D(float("inf")), GOOD4, None, D(0),
+                 None) == -1
+
+
+def test_spinor_marshalling_roundtrip():
+    """Real r = 2*(3*alpha + a) + part of site n sits at ((r/W)*V + n)*W + r%W."""
+    lat = lqcd.Lattice.symanzik((2, 3, 2, 2))
+    x = np.arange(lat.V * 24, dtype=np.float64).reshape(lat.V, 4, 3, 2)
+    for prec in ("f32", "f64"):
+        L2 = lat.with_(precision=prec)
+        t = lqcd.spinor_to_device(L2, x, device="cpu")
+        assert tuple(t.shape) == L2.spinor_shape
+        flat = t.numpy().ravel()
+        W = L2.W
+        for n, al, a, part in [(0, 0, 0, 0), (5, 2, 1, 1), (23, 3, 2, 1), (7, 1, 2, 0)]:
+            r = 2 * (3 * al + a) + part
+            assert flat[((r // W) * lat.V + n) * W + r % W] == x[n, al, a, part]
+        back = lqcd.spinor_from_device(t)
+        np.testing.assert_array_equal(back, x[..., 0] + 1j * x[..., 1])
+
+
 def test_strerror(lib):
     assert lib.lqcd_strerror(0) == b"success"
     for code in range(-7, 0):

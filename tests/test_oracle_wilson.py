@@ -127,7 +127,6 @@ def test_hopping_force_is_minus_the_gradient(cfg):
     (the left Lie derivative), by central differences on 96 links x 8."""
     U, X, Y = cfg
     h = O.wilson_hopping_force(DIMS, U, X, Y)
-    T = H.gell_mann() / 2
     eps = 1e-5
     links = synth.sample_links(V * 4, 96, seed=2)
     worst = 0.0
@@ -145,7 +144,12 @@ def test_hopping_force_is_minus_the_gradient(cfg):
 
 
 def test_hopping_force_link_and_scale(cfg):
+    """The one-link and one-site forms equal the whole-lattice ones; coef
+    scales the force."""
     U, X, Y = cfg
+    D = O.wilson_hopping(DIMS, U, X)
+    for n in (0, 37, 255):
+        np.testing.assert_array_equal(O.wilson_hopping_site(DIMS, U, X, n), D[n])
     h = O.wilson_hopping_force(DIMS, U, X, Y)
     for li in synth.sample_links(V * 4, 16, seed=9):
         k, rho = divmod(int(li), 4)
