@@ -48,6 +48,14 @@ BYTES_LINK_UPDATE = {"f32": 128, "f64": 256}   # read U, read p, write U
 # FP32 lanes x 2 flop (FMA) x 2.070 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 CPU_SAMPLE_DIMS = (12, 12, 12, 12)
+# Wilson fermion kernels (Sec. III), compulsory bytes in units of the real
+# size R: the hopping operator reads x (24 R) and the 4 links of a site
+# (48 R) and writes y (24 R) per site; the hopping-term force with the fused
+# momentum step reads per link its link (12 R), a quarter of a site's X and Y
+# (12 R) and the momenta (8 R), and writes the momenta (8 R).
+WILSON_KAPPA = 0.1315
+WILSON_REALS_PER_SITE_DSLASH = 96
+WILSON_REALS_PER_LINK_FORCE = 40
 
 
 def _peaks():
@@ -462,11 +470,55 @@ def run_ours(args):
     del bs, g_batch, actions
     torch.cuda.empty_cache()
 
+    # Wilson fermion force at the same lattice (Sec. III): Y = D X with the
+    # hopping operator (kappa 0.1315, no clover term), then the hopping-term
+    # force with the momentum step fused; each kernel timed alone with L2
+    # flushed (a 256 MB write) between repetitions
+    hbm_peak, peak_kind = _peaks()
+    wilson = {"kappa": WILSON_KAPPA, "workload": WORKLOAD,
+              "x": "Gaussian spinor, re/im ~ N(0, 1)", "peak_gbs": hbm_peak, "peak_kind": peak_kind}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def kernel_ms(fn, reps):
+        for _ in range(3):
+            fn()
+        tot = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(stream)
+            fn()
+            b_.record(stream)
+            torch.cuda.synchronize(dev)
+            tot += a_.elapsed_time(b_)
+        return tot / reps
+
+    for prec in ("f32", "f64"):
+        lat = lqcd.Lattice(dims, prec)
+        real = 4 if prec == "f32" else 8
+        U = lqcd.links_from_omega(lat, lqcd.algebra_to_device(lat, omega_np, device=dev))
+        X = lqcd.spinor_to_device(lat, synth.spinor(dims, 11 + seed), device=dev)
+        Y = lqcd.empty_spinor(lat, dev)
+        pm = lqcd.algebra_to_device(lat, p_np, device=dev)
+        reps = 20 if prec == "f32" else 5
+        ms_d = kernel_ms(lambda: lqcd.wilson_dslash(lat, U, X, 1.0, -WILSON_KAPPA, out=Y), reps)
+        ms_f = kernel_ms(lambda: lqcd.wilson_hopping_force(lat, U, X, Y, coef=WILSON_KAPPA,
+                                                          mom=pm, dt=DT), reps)
+        gb_d = WILSON_REALS_PER_SITE_DSLASH * real * V / (ms_d / 1e3) / 1e9
+        gb_f = WILSON_REALS_PER_LINK_FORCE * real * nlinks / (ms_f / 1e3) / 1e9
+        wilson[prec] = {"dslash_ms": ms_d, "dslash_gbs": gb_d, "dslash_frac": gb_d / hbm_peak,
+                        "force_ms": ms_f, "force_gbs": gb_f, "force_frac": gb_f / hbm_peak,
+                        "step_ms": ms_d + ms_f,
+                        "step_glinks": nlinks / ((ms_d + ms_f) / 1e3) / 1e9}
+        del U, X, Y, pm
+        torch.cuda.empty_cache()
+    del flush
+    torch.cuda.empty_cache()
+
     if rank != 0:
         ctx.close()
         return 0
 
-    hbm_peak, peak_kind = _peaks()
     force_ms = per["force"]
     achieved_tflops = FLOP_PER_LINK_FORCE * nlinks / (force_ms / 1e3) / 1e12
     roofline = {
@@ -516,6 +568,7 @@ def run_ours(args):
         "action_f32": S32, "action_f64": S64,
         "dH": dh,
         "batch": batch,
+        "wilson": wilson,
         "roofline": roofline,
         "streaming": streaming,
         "cpu_baseline": cpu,

@@ -222,9 +222,15 @@ __device__ __forceinline__ void hop(Spinor<R> &acc, const R *__restrict__ links,
 
 constexpr int kDslashBlock = 128;
 
+// Register cap: 4 blocks (16 warps) per SM in FP32, measured 17 % faster at
+// 32^3x64 than the uncapped 138 registers (12 warps), without spills; FP64
+// is bound by the FP64 pipe and keeps its registers.
+template <typename R> constexpr int dslash_min_blocks() { return sizeof(R) == 8 ? 1 : 4; }
+
 // out_n = ca x_n + cb (calD x)_n, one thread per site.
 template <typename R>
-__global__ void __launch_bounds__(kDslashBlock) wilson_dslash(const __grid_constant__ WilsonArgs a)
+__global__ void __launch_bounds__(kDslashBlock, dslash_min_blocks<R>())
+    wilson_dslash(const __grid_constant__ WilsonArgs a)
 {
     const Geom g = make_geom(a.dims);
     const R *__restrict__ links = static_cast<const R *>(a.links);
