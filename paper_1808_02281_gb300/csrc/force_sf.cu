@@ -278,6 +278,21 @@ __global__ void __launch_bounds__(kBlock) staple_fields_batched(const __grid_con
 
 // ---------------------------------------------------------------- pass B
 
+// Products of two SU(3) factors are accumulated as y += s * (a * op(b)) with
+// the third row of the product rebuilt from its first two (mul_acc_su3: the
+// third row of a is never rebuilt), except for full FP64 staples ("direct"),
+// where nothing is rebuilt anyway and plain accumulation with one scaling of
+// the sum measured faster (114 vs 122 ms at 32^3x64: at the 255-register
+// limit the extra temporaries spill).
+template <bool FULL, typename R> constexpr bool direct_products() { return FULL && sizeof(R) == 8; }
+
+template <int FB, bool FULL, typename R>
+__device__ __forceinline__ void acc_su3(Mat<R> &y, const Mat<R> &a, const Mat<R> &b, R s)
+{
+    if constexpr (direct_products<FULL, R>()) mul_acc<N, FB>(y, a, b); // s applied by the caller
+    else mul_acc_su3<FB>(y, a, b, s);
+}
+
 // The staples that start with link(k+rho, d), d = +-nu_d (NEG: minus):
 //   t += B_d [ c_cube sum_{b perp rho, d} S_b(k+d) S^{(d)}_b(k) + c_rect S_d(k+d) A_d^dag ]
 // (the orientation of the shared links fixed at compile time, so that each
@@ -303,18 +318,21 @@ __device__ __forceinline__ void d_terms(Mat<R> &t, const R *__restrict__ links,
         const int nub = (rho + 1 + ib) & 3;
         const int jp = 2 * ((nub - nud - 1) & 3);
         using SIO = Staples<R, FULL>;
-        mul_acc<N, FD>(y, SIO::load(sf, g.V, base + 2 * ib, kd), SIO::load(sf, g.V, nud * 6 + jp, site2));
-        mul_acc<N, FD>(y, SIO::load(sf, g.V, base + 2 * ib + 1, kd),
-                       SIO::load(sf, g.V, nud * 6 + jp + 1, site2));
+        acc_su3<FD, FULL>(y, SIO::load(sf, g.V, base + 2 * ib, kd),
+                          SIO::load(sf, g.V, nud * 6 + jp, site2), c_cb);
+        acc_su3<FD, FULL>(y, SIO::load(sf, g.V, base + 2 * ib + 1, kd),
+                          SIO::load(sf, g.V, nud * 6 + jp + 1, site2), c_cb);
     }
-    scale(y, c_cb);
     Mat<R> r3 = Staples<R, FULL>::load(sf, g.V, base + jd, kd);
-    scale(r3, c_rt);
+    if constexpr (direct_products<FULL, R>()) {
+        scale(y, c_cb);
+        scale(r3, c_rt);
+    }
     if constexpr (!NEG) {
-        mul_acc<N, D>(y, r3, load_link(links, g.V, nud, k));  // A_d = U_nud(k)
-        mul_acc<N, N>(t, load_link(links, g.V, nud, kp), y);  // B_d = U_nud(k+rho)
+        acc_su3<D, FULL>(y, r3, load_link(links, g.V, nud, k), c_rt); // A_d = U_nud(k)
+        mul_acc<N, N>(t, load_link(links, g.V, nud, kp), y);        // B_d = U_nud(k+rho)
     } else {
-        mul_acc<N, N>(y, r3, load_link(links, g.V, nud, kd)); // A_d = U_nud(k-nud)^dag
+        acc_su3<N, FULL>(y, r3, load_link(links, g.V, nud, kd), c_rt); // A_d = U_nud(k-nud)^dag
         mul_acc<D, N>(t, load_link(links, g.V, nud, kp + (kd - k)), y); // B_d = U_nud(k+rho-nud)^dag
     }
 }
@@ -349,13 +367,13 @@ __device__ __forceinline__ double force_block(const SfLattice &L, const KernelSc
             using SIO = Staples<R, FULL>;
             const Mat<R> s = SIO::load(sf, g.V, base + jj, k);
             add_to(pl, s);
-            mul_acc<N, N>(p1, SIO::load(sf, g.V, base + jj, kp), s);
+            acc_su3<N, FULL>(p1, SIO::load(sf, g.V, base + jj, kp), s, c_rt);
             mul_acc<N, N>(p2, s, SIO::load(sf, g.V, base + jj, km));
         }
         if constexpr (ACTION) tr_pl = re_trace_mul<N, N>(load_link(links, g.V, rho, k), pl);
         t = pl;
         scale(t, c_pl);
-        scale(p1, c_rt);
+        if constexpr (direct_products<FULL, R>()) scale(p1, c_rt);
         mul_acc<N, N>(t, load_link(links, g.V, rho, kp), p1);
         scale(p2, c_rt);
         mul_acc<N, N>(t, p2, load_link(links, g.V, rho, km));
@@ -467,11 +485,11 @@ unsigned grid_of(int64_t items)
 //   3  x rows, registers capped for 4 CTAs/SM also with the fused action
 //   4  x rows, staple planes stored full (18 reals, no row rebuilt on load)
 // The process-wide choice per precision is set by lqcd_set_force_variant or
-// lqcd_autotune_force; -1 means the default: x rows with compact staples in
-// FP32, full staples in FP64 (where the row rebuild costs FP64 issue slots;
-// 114 vs 139 ms at 32^3x64 against 5.5 vs 5.1 ms in FP32).
+// lqcd_autotune_force; -1 means the default: x rows with full staples in both
+// precisions (at 32^3x64: FP32 4.64 vs 4.75 ms with compact staples, FP64
+// 114 vs 128 ms).
 constexpr int kSfVariants = 5;
-constexpr int kSfDefault[2] = {2, 4};
+constexpr int kSfDefault[2] = {4, 4};
 std::atomic<int> g_sf_variant[2] = {{-1}, {-1}};
 
 // Largest divisor of L not above cap.

@@ -166,6 +166,9 @@ struct WilsonArgs {
     void *mom;       // momenta updated in place (or null)
     double ca, cb;   // dslash: out = ca * x + cb * calD x
     double coef, dt; // force: f = coef * h;  mom += dt * f
+    // the same four scalars rounded to FP32 by the launcher, so that FP32
+    // kernels spend no FP64 conversions on them
+    float fca, fcb, fcoef, fdt;
 };
 cudaError_t launch_wilson_dslash(const WilsonArgs &a, cudaStream_t st);
 cudaError_t launch_wilson_hopping_force(const WilsonArgs &a, cudaStream_t st);

@@ -212,6 +212,26 @@ template <typename R> __device__ __forceinline__ void rebuild_row2(Mat<R> &u)
 #undef LQCD_CROSS
 }
 
+// y += s * (a * op_b(b)) for a, b in SU(3): rows 0 and 1 of the product
+// come from rows 0 and 1 of a, and its third row is conj(row0 x row1) of the
+// product (a product of SU(3) matrices is in SU(3)).  The third row of a is
+// never read, so for a compact link or staple its rebuild is dead code:
+// 96 instead of 132 flops per product.
+template <int FB, typename R>
+__device__ __forceinline__ void mul_acc_su3(Mat<R> &y, const Mat<R> &a, const Mat<R> &b,
+                                            R s = R(1))
+{
+    Mat<R> p = mul_top2<N, FB>(a, b);
+    rebuild_row2(p);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            y.re[i][j] = fma(s, p.re[i][j], y.re[i][j]);
+            y.im[i][j] = fma(s, p.im[i][j], y.im[i][j]);
+        }
+}
+
 // ------------------------------------------------------------- link I/O
 
 // Link layout: real r of link (n, mu) at ((mu*(12/W) + r/W)*V + n)*W + r%W.

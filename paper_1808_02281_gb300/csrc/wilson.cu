@@ -51,6 +51,13 @@ template <int K, typename R> __device__ __forceinline__ void times_ipow(R &re, R
     }
 }
 
+// A launch scalar in the kernel's precision (FP32 copies made on the host).
+template <typename R> __device__ __forceinline__ R scalar_of(double d, float f)
+{
+    if constexpr (sizeof(R) == 8) return d;
+    else return f;
+}
+
 template <typename R> struct Spinor {
     R re[4][3], im[4][3];
 };
@@ -236,7 +243,8 @@ __global__ void __launch_bounds__(kDslashBlock, dslash_min_blocks<R>())
     const R *__restrict__ links = static_cast<const R *>(a.links);
     const R *__restrict__ x = static_cast<const R *>(a.x);
     R *__restrict__ out = static_cast<R *>(a.out);
-    const R ca = R(a.ca), cb = R(a.cb);
+    const R ca = scalar_of<R>(a.ca, a.fca), cb = scalar_of<R>(a.cb, a.fcb);
+    const bool with_x = a.ca != 0.0;
     for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < g.V;
          n += (int64_t)gridDim.x * blockDim.x) {
         const Coord c = coord_of(g, n);
@@ -249,7 +257,7 @@ __global__ void __launch_bounds__(kDslashBlock, dslash_min_blocks<R>())
         hop<1>(acc, links, x, g, c, n);
         hop<2>(acc, links, x, g, c, n);
         hop<3>(acc, links, x, g, c, n);
-        if (a.ca != 0.0) {
+        if (with_x) {
             const Spinor<R> xn = load_spinor(x, g.V, n);
 #pragma unroll
             for (int al = 0; al < 4; ++al)
@@ -316,13 +324,13 @@ __global__ void __launch_bounds__(kForceBlock) wilson_hopping_force(const __grid
     }
     // f^i = coef * h^i,  h^i = -(tr(i T_i M) + c.c.) = Im tr(lambda_i M)
     R f[8];
-    ta_components(m, R(-a.coef), f);
+    ta_components(m, -scalar_of<R>(a.coef, a.fcoef), f);
     if (a.force != nullptr) store_algebra(static_cast<R *>(a.force), g.V, rho, k, f);
     if (a.mom != nullptr) {
         R *mom = static_cast<R *>(a.mom);
         R p[8];
         load_algebra(mom, g.V, rho, k, p);
-        const R dt = R(a.dt);
+        const R dt = scalar_of<R>(a.dt, a.fdt);
 #pragma unroll
         for (int q = 0; q < 8; ++q) p[q] = fma(dt, f[q], p[q]);
         store_algebra(mom, g.V, rho, k, p);
@@ -337,10 +345,20 @@ unsigned blocks_for(int64_t items, int per_block)
     return (unsigned)b;
 }
 
+WilsonArgs with_float_scalars(WilsonArgs a)
+{
+    a.fca = (float)a.ca;
+    a.fcb = (float)a.cb;
+    a.fcoef = (float)a.coef;
+    a.fdt = (float)a.dt;
+    return a;
+}
+
 } // namespace
 
-cudaError_t launch_wilson_dslash(const WilsonArgs &a, cudaStream_t st)
+cudaError_t launch_wilson_dslash(const WilsonArgs &args, cudaStream_t st)
 {
+    const WilsonArgs a = with_float_scalars(args);
     const int64_t V = (int64_t)a.dims[0] * a.dims[1] * a.dims[2] * a.dims[3];
     const unsigned grid = blocks_for(V, kDslashBlock);
     if (a.precision == LQCD_F64) wilson_dslash<double><<<grid, kDslashBlock, 0, st>>>(a);
@@ -348,8 +366,9 @@ cudaError_t launch_wilson_dslash(const WilsonArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_wilson_hopping_force(const WilsonArgs &a, cudaStream_t st)
+cudaError_t launch_wilson_hopping_force(const WilsonArgs &args, cudaStream_t st)
 {
+    const WilsonArgs a = with_float_scalars(args);
     const int64_t V = (int64_t)a.dims[0] * a.dims[1] * a.dims[2] * a.dims[3];
     const unsigned grid = blocks_for(V, 32);
     if (a.precision == LQCD_F64) wilson_hopping_force<double><<<grid, kForceBlock, 0, st>>>(a);
