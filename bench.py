@@ -10,6 +10,7 @@ Inputs (403 MB of links, 268 MB of momenta, 268 MB of force) are larger
 than the 129 MB L2, so no flush is needed between steps.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--force-variant V]
 N > 1 runs as independent replicas, one lattice per rank (the path has no
 exchange step on one lattice per GPU); value = links of all ranks / max time.
 --impl reference times the FP64 CPU oracle on the host cores instead.
@@ -299,9 +300,14 @@ def run_ours(args):
 
     def timed(prec, K, W, with_events):
         lat, U, mom, force, S, ws = make(prec)
-        # set-up, untimed: pick the fastest force schedule on these links
-        best, ms_v = lqcd.autotune_force(lat, U, reps=3, workspace=ws)
-        tuned[prec] = {"variant": best, "ms_per_variant": ms_v}
+        # set-up, untimed: pick the fastest force schedule on these links, or
+        # take the one fixed on the command line (reproducible profiling)
+        if args.force_variant >= 0:
+            lqcd.set_force_variant(lat, args.force_variant)
+            tuned[prec] = {"variant": args.force_variant, "fixed": True}
+        else:
+            best, ms_v = lqcd.autotune_force(lat, U, reps=3, workspace=ws)
+            tuned[prec] = {"variant": best, "ms_per_variant": ms_v}
         for _ in range(W):
             step(lat, U, mom, force, S, ws)
         torch.cuda.synchronize(dev)
@@ -589,6 +595,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--force-variant", type=int, default=-1,
+                    help="fix the staple-field force schedule (0..4) instead of autotuning it "
+                         "at set-up; -1 (default) autotunes")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -184,3 +184,47 @@ def test_hopping_force_swaps_under_adjoint(cfg):
     b = O.wilson_hopping_force(DIMS, U, np.einsum("ab,nbc->nac", g5, X),
                                np.einsum("ab,nbc->nac", g5, Y))
     assert np.abs(a - b).max() < 1e-12 * np.abs(a).max()
+
+
+def test_fermion_action_derivative_chain():
+    """Eq. 18_6_24_0 end to end on a 3x2x2x2 lattice (288 unknowns):
+    S_F(U) = phi^dag (D^dag D)^{-1} phi with D = 1 - kappa calD built densely
+    from the oracle's calD, phi fixed.  At X = (D^dag D)^{-1} phi, Y = D X,
+    -dS_F/domega^i_{k,rho} (central differences of a direct solve) equals
+    kappa h^i(X, Y): the hopping force with coef = kappa."""
+    dims = (3, 2, 2, 2)
+    Vd = int(np.prod(dims))
+    kappa = 0.12
+    U0 = O.links_from_omega(synth.omega(dims, 0.6, 21))
+
+    def dmat(U):
+        n = Vd * 12
+        cols = []
+        for j in range(n):
+            e = np.zeros(n, dtype=np.complex128)
+            e[j] = 1.0
+            cols.append(e - kappa * O.wilson_hopping(dims, U, e.reshape(Vd, 4, 3)).ravel())
+        return np.stack(cols, axis=1)
+
+    D0 = dmat(U0)
+    X = _spinor(dims, 31)
+    phi = D0.conj().T @ (D0 @ X.ravel())
+    Y = (D0 @ X.ravel()).reshape(Vd, 4, 3)
+    h = O.wilson_hopping_force(dims, U0, X, Y, kappa)
+
+    def s_f(U):
+        D = dmat(U)
+        return np.vdot(phi, np.linalg.solve(D.conj().T @ D, phi)).real
+
+    eps = 1e-5
+    worst = 0.0
+    for k, rho in [(0, 0), (5, 3), (17, 1), (23, 2)]:
+        for a in range(8):
+            d = []
+            for sgn in (1, -1):
+                U = U0.copy()
+                U[k, rho] = O.exp_i_algebra(sgn * eps * np.eye(8)[a]) @ U0[k, rho]
+                d.append(s_f(U))
+            fd = -(d[0] - d[1]) / (2 * eps)
+            worst = max(worst, abs(fd - h[k, rho, a]))
+    assert worst < 1e-6 * np.abs(h).max(), worst
