@@ -476,6 +476,14 @@ def run_ours(args):
     del bs, g_batch, actions
     torch.cuda.empty_cache()
 
+    # the device: SM count, L2, and the measured FMA issue rates (FP32, FP64)
+    props = torch.cuda.get_device_properties(dev)
+    device = {"name": props.name, "sms": props.multi_processor_count,
+              "l2_mb": getattr(props, "L2_cache_size", 0) / 2**20,
+              "fma_tflops_f32": lqcd.measure_fma_rate("f32", device=dev),
+              "fma_tflops_f64": lqcd.measure_fma_rate("f64", device=dev),
+              "fma_note": "measured: every SM filled with independent FMA chains (lqcd_measure_fma_rate)"}
+
     # Wilson fermion force at the same lattice (Sec. III): Y = D X with the
     # hopping operator (kappa 0.1315, no clover term), then the hopping-term
     # force with the momentum step fused; each kernel timed alone with L2
@@ -575,6 +583,7 @@ def run_ours(args):
         "dH": dh,
         "batch": batch,
         "wilson": wilson,
+        "device": device,
         "roofline": roofline,
         "streaming": streaming,
         "cpu_baseline": cpu,

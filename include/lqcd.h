@@ -315,6 +315,20 @@ LQCD_API int lqcd_wilson_hopping_force(const lqcd_desc *desc, const void *links,
                                        const void *Y, double coef, void *force, void *mom,
                                        double dt, void *stream);
 
+/* ------------------------------------------------------------ diagnostics
+ *
+ * lqcd_measure_fma_rate: the FP32 (precision LQCD_F32) or FP64 (LQCD_F64)
+ * FMA issue rate of the current device in TFLOP/s (2 flops per FMA), from a
+ * grid that fills every SM with independent FMA chains, timed with CUDA
+ * events on `stream` (about 20 ms; synchronises the stream).  The
+ * denominators of the ALU-bound force kernels; the paper has no
+ * counterpart.  scratch: device, >= lqcd_fma_rate_scratch_bytes() bytes,
+ * overwritten.  Returns LQCD_ERR_ARG on a bad precision or NULL output,
+ * LQCD_ERR_WORKSPACE if scratch is missing or too small. */
+LQCD_API int lqcd_measure_fma_rate(int precision, void *scratch, size_t scratch_bytes,
+                                   double *tflops, void *stream);
+LQCD_API size_t lqcd_fma_rate_scratch_bytes(void);
+
 /* Bytes of device workspace that this descriptor needs on the current
  * device: the staple planes and action partials of the staple-field force
  * (force_algo STAPLE_FIELDS or AUTO; 24 SU(3) planes per site -- 1920 bytes

@@ -517,6 +517,18 @@ int lqcd_wilson_hopping_force(const lqcd_desc *desc, const void *links, const vo
     return cuda_status(lqcd::launch_wilson_hopping_force(w, as_stream(stream)));
 }
 
+int lqcd_measure_fma_rate(int precision, void *scratch, size_t scratch_bytes, double *tflops,
+                          void *stream)
+{
+    if ((precision != LQCD_F32 && precision != LQCD_F64) || tflops == nullptr) return LQCD_ERR_ARG;
+    if (scratch == nullptr || scratch_bytes < lqcd::fma_rate_scratch_bytes() || !aligned16(scratch))
+        return LQCD_ERR_WORKSPACE;
+    return cuda_status(lqcd::measure_fma_rate(precision, scratch, scratch_bytes, tflops,
+                                              as_stream(stream)));
+}
+
+size_t lqcd_fma_rate_scratch_bytes(void) { return lqcd::fma_rate_scratch_bytes(); }
+
 static int convert_common(const lqcd_desc *desc, const void *src, int dst_precision, void *dst,
                           bool links, void *stream)
 {

@@ -484,11 +484,22 @@ unsigned grid_of(int64_t items)
 //   2  x rows (no micro-tiles), inner b loop rolled
 //   3  x rows, registers capped for 4 CTAs/SM also with the fused action
 //   4  x rows, staple planes stored full (18 reals, no row rebuilt on load)
+//   5  x rows, full staple planes, registers capped for 4 CTAs/SM
 // The process-wide choice per precision is set by lqcd_set_force_variant or
 // lqcd_autotune_force; -1 means the default: x rows with full staples in both
 // precisions (at 32^3x64: FP32 4.64 vs 4.75 ms with compact staples, FP64
 // 114 vs 128 ms).
-constexpr int kSfVariants = 5;
+constexpr int kSfVariants = 6;
+
+bool full_staples(int variant) { return variant == 4 || variant == 5; }
+
+// Slot of a kernel instance in the occupancy cache of persistent_grid:
+// kind (0 pass B, 1 pass B capped, 2 pass B full, 3 pass B full capped,
+// 4 pass A compact, 5 pass A full) x precision x action x unrolled.
+int grid_slot(int kind, bool f64, bool action, bool unrolled)
+{
+    return kind * 8 + (f64 ? 4 : 0) + (action ? 2 : 0) + (unrolled ? 1 : 0);
+}
 constexpr int kSfDefault[2] = {4, 4};
 std::atomic<int> g_sf_variant[2] = {{-1}, {-1}};
 
@@ -505,7 +516,7 @@ void set_traversal(SfLattice &L, int variant)
     L.sweep[0] = block_extent(L.dims[0], 64);
     L.sweep[1] = block_extent(L.dims[1], 16);
     L.sweep[2] = block_extent(L.dims[2], 16);
-    if (variant == 2 || variant == 3 || variant == 4) {
+    if (variant >= 2) {
         L.micro[0] = L.sweep[0];
         L.micro[1] = L.micro[2] = 1;
     } else {
@@ -541,7 +552,7 @@ int resolve_variant(const ForceArgs &a)
 template <typename K> unsigned persistent_grid(K kernel, int slot, int64_t work)
 {
     static std::mutex mu;
-    static int cached[64][32] = {{0}};
+    static int cached[64][48] = {{0}};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return grid_of(work);
     int resident = 0;
@@ -566,6 +577,8 @@ cudaError_t launch_pass_b(const SfLattice &L, const KernelScalars &sc, int varia
     else if (variant == 3) force_from_staples<R, ACTION, false, true><<<grid, kBlock, 0, st>>>(L, sc);
     else if (variant == 4)
         force_from_staples<R, ACTION, false, false, true><<<grid, kBlock, 0, st>>>(L, sc);
+    else if (variant == 5)
+        force_from_staples<R, ACTION, false, true, true><<<grid, kBlock, 0, st>>>(L, sc);
     else force_from_staples<R, ACTION, false><<<grid, kBlock, 0, st>>>(L, sc);
     return cudaGetLastError();
 }
@@ -574,19 +587,22 @@ template <typename R, bool ACTION>
 cudaError_t launch_pass_b_batched(const SfBatch &B, const KernelScalars &sc, int variant,
                                   cudaStream_t st)
 {
-    const int slot = (sizeof(R) == 8 ? 4 : 0) + (ACTION ? 2 : 0) + (variant == 1 ? 1 : 0);
+    constexpr bool f64 = sizeof(R) == 8;
     if (variant == 1) {
         auto k = force_from_staples_batched<R, ACTION, true>;
-        k<<<persistent_grid(k, slot, B.total), kBlock, 0, st>>>(B, sc);
+        k<<<persistent_grid(k, grid_slot(0, f64, ACTION, true), B.total), kBlock, 0, st>>>(B, sc);
     } else if (variant == 3) {
         auto k = force_from_staples_batched<R, ACTION, false, true>;
-        k<<<persistent_grid(k, 8 + slot, B.total), kBlock, 0, st>>>(B, sc);
+        k<<<persistent_grid(k, grid_slot(1, f64, ACTION, false), B.total), kBlock, 0, st>>>(B, sc);
     } else if (variant == 4) {
         auto k = force_from_staples_batched<R, ACTION, false, false, true>;
-        k<<<persistent_grid(k, 16 + slot, B.total), kBlock, 0, st>>>(B, sc);
+        k<<<persistent_grid(k, grid_slot(2, f64, ACTION, false), B.total), kBlock, 0, st>>>(B, sc);
+    } else if (variant == 5) {
+        auto k = force_from_staples_batched<R, ACTION, false, true, true>;
+        k<<<persistent_grid(k, grid_slot(3, f64, ACTION, false), B.total), kBlock, 0, st>>>(B, sc);
     } else {
         auto k = force_from_staples_batched<R, ACTION, false>;
-        k<<<persistent_grid(k, slot, B.total), kBlock, 0, st>>>(B, sc);
+        k<<<persistent_grid(k, grid_slot(0, f64, ACTION, false), B.total), kBlock, 0, st>>>(B, sc);
     }
     return cudaGetLastError();
 }
@@ -605,7 +621,7 @@ template <typename R> cudaError_t launch_sf_t(const ForceArgs &a, cudaStream_t s
     L.action = a.action;
     const KernelScalars sc = make_scalars(a);
     const int64_t nvb = virtual_blocks((int64_t)a.dims[0] * a.dims[1] * a.dims[2] * a.dims[3]);
-    if (variant == 4) staple_fields<R, true><<<grid_of(nvb), kBlock, 0, st>>>(L);
+    if (full_staples(variant)) staple_fields<R, true><<<grid_of(nvb), kBlock, 0, st>>>(L);
     else staple_fields<R, false><<<grid_of(nvb), kBlock, 0, st>>>(L);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -639,12 +655,12 @@ cudaError_t launch_sf_batched_t(const ForceArgs &a, int n, const SfLattice *item
     const KernelScalars sc = make_scalars(a);
     cudaError_t e = cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    if (variant == 4) {
+    if (full_staples(variant)) {
         auto ka = staple_fields_batched<R, true>;
-        ka<<<persistent_grid(ka, 24 + (sizeof(R) == 8 ? 4 : 0), B.total), kBlock, 0, st>>>(B);
+        ka<<<persistent_grid(ka, grid_slot(5, sizeof(R) == 8, false, false), B.total), kBlock, 0, st>>>(B);
     } else {
         auto ka = staple_fields_batched<R, false>;
-        ka<<<persistent_grid(ka, 3 + (sizeof(R) == 8 ? 4 : 0), B.total), kBlock, 0, st>>>(B);
+        ka<<<persistent_grid(ka, grid_slot(4, sizeof(R) == 8, false, false), B.total), kBlock, 0, st>>>(B);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

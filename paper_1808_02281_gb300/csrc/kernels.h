@@ -171,6 +171,10 @@ struct WilsonArgs {
     float fca, fcb, fcoef, fdt;
 };
 cudaError_t launch_wilson_dslash(const WilsonArgs &a, cudaStream_t st);
+// FMA issue rate of the device in TFLOP/s (synchronises); scratch >= fma_rate_scratch_bytes().
+cudaError_t measure_fma_rate(int precision, void *scratch, size_t scratch_bytes, double *tflops,
+                             cudaStream_t st);
+size_t fma_rate_scratch_bytes();
 cudaError_t launch_wilson_hopping_force(const WilsonArgs &a, cudaStream_t st);
 
 } // namespace lqcd

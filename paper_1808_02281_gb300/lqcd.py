@@ -87,6 +87,9 @@ _EXPORTS = {
     "lqcd_wilson_hopping_force": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
                                                  ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]),
+    "lqcd_measure_fma_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
+                                             ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "lqcd_fma_rate_scratch_bytes": (ctypes.c_size_t, []),
     "lqcd_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(Desc)]),
     "lqcd_workspace_bytes_batched": (ctypes.c_size_t, [ctypes.POINTER(Desc), ctypes.c_int,
                                                        ctypes.POINTER(LatticeRef)]),
@@ -262,6 +265,17 @@ def wilson_hopping_force(lat: Lattice, links: torch.Tensor, X: torch.Tensor, Y: 
           float(coef), None if force is None else _ptr(force),
           None if mom is None else _ptr(mom), float(dt), _stream(stream))
     return force
+
+
+def measure_fma_rate(precision: str = "f32", device=None, stream=None) -> float:
+    """FMA issue rate of the device in TFLOP/s (FP32 or FP64; ~20 ms,
+    synchronises)."""
+    n = int(_lib().lqcd_fma_rate_scratch_bytes())
+    scratch = torch.empty(n, dtype=torch.uint8, device=device or "cuda")
+    out = ctypes.c_double()
+    _call("lqcd_measure_fma_rate", F32 if precision == "f32" else F64, _ptr(scratch), n,
+          ctypes.byref(out), _stream(stream))
+    return out.value
 
 
 def workspace_bytes(lat: Lattice) -> int:

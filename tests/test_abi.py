@@ -130,6 +130,17 @@ def test_wilson_argument_checks(lib):
                  None) == -1
 
 
+def test_fma_rate_argument_checks(lib):
+    out = ctypes.c_double()
+    n = lib.lqcd_fma_rate_scratch_bytes()
+    assert n >= 1 << 20
+    assert lib.lqcd_measure_fma_rate(7, GOOD, n, ctypes.byref(out), None) == -1
+    assert lib.lqcd_measure_fma_rate(0, GOOD, n, None, None) == -1
+    assert lib.lqcd_measure_fma_rate(0, None, n, ctypes.byref(out), None) == -4
+    assert lib.lqcd_measure_fma_rate(1, GOOD, n - 1, ctypes.byref(out), None) == -4
+    assert lib.lqcd_measure_fma_rate(1, MISALIGNED, n, ctypes.byref(out), None) == -4
+
+
 def test_spinor_marshalling_roundtrip():
     """Real r = 2*(3*alpha + a) + part of site n sits at ((r/W)*V + n)*W + r%W."""
     lat = lqcd.Lattice.symanzik((2, 3, 2, 2))
