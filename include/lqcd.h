@@ -331,7 +331,7 @@ LQCD_API size_t lqcd_fma_rate_scratch_bytes(void);
 
 /* Bytes of device workspace that this descriptor needs on the current
  * device: the staple planes and action partials of the staple-field force
- * (force_algo STAPLE_FIELDS or AUTO; 24 SU(3) planes per site -- 1920 bytes
+ * (force_algo STAPLE_FIELDS or AUTO; 24 SU(3) planes per site -- 1728 bytes
  * in FP32, 3456 in FP64, room for either storage form -- plus one double per
  * 32 sites) and the partial sums of lqcd_gauge_action / lqcd_kinetic_energy
  * (0 on a bad descriptor). */

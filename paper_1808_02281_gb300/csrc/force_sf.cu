@@ -65,13 +65,24 @@ template <typename R> __device__ __forceinline__ R scalar(const KernelScalars &s
     else return s.d[i];
 }
 
-// Storage of the staple planes: compact (rows 0 and 1, 12 reals, the third
-// row rebuilt on load, as for links) or full (all 18 reals in ceil(18/W)
-// lanes, nothing rebuilt: 1.67x the bytes in FP32, fewer instructions).
+// Storage of the 24 staple planes: compact (rows 0 and 1, 12 reals, the
+// third row rebuilt on load, as for links) or full (all 18 reals, nothing
+// rebuilt).  Full planes hold 18/W whole 16-byte lanes per plane, plane P's
+// lane q at ((P*NW + q)*V + n); in FP32 the last two reals of every plane go
+// to a float2 region after all 24*4 lanes, at (P*V + n): 72 bytes per staple
+// instead of 80, with every load and store still 16- or 8-byte aligned.
+constexpr int kStaplePlanes = 24;
+
 template <typename R, bool FULL> struct Staples {
     using V4 = typename Vec<R>::type;
     static constexpr int W = Vec<R>::W;
-    static constexpr int LANES = FULL ? (18 + W - 1) / W : 12 / W;
+    static constexpr int NW = FULL ? 18 / W : 12 / W; // whole lanes per plane
+    static constexpr int TAIL = FULL ? 18 - NW * W : 0; // reals in the float2 region (FP32 full: 2)
+
+    static __device__ __forceinline__ const float2 *tail(const R *sf, int64_t V)
+    {
+        return reinterpret_cast<const float2 *>(sf + (int64_t)kStaplePlanes * NW * W * V);
+    }
 
     static __device__ __forceinline__ Mat<R> load(const R *__restrict__ sf, int64_t V, int plane,
                                                   int64_t n)
@@ -79,10 +90,10 @@ template <typename R, bool FULL> struct Staples {
         if constexpr (!FULL) {
             return load_link(sf, V, plane, n);
         } else {
-            const V4 *p = reinterpret_cast<const V4 *>(sf) + (int64_t)plane * LANES * V + n;
-            R r[LANES * W];
+            const V4 *p = reinterpret_cast<const V4 *>(sf) + (int64_t)plane * NW * V + n;
+            R r[18];
 #pragma unroll
-            for (int q = 0; q < LANES; ++q) {
+            for (int q = 0; q < NW; ++q) {
                 const V4 v = __ldg(p + q * V);
                 if constexpr (W == 4) {
                     r[4 * q + 0] = v.x;
@@ -93,6 +104,11 @@ template <typename R, bool FULL> struct Staples {
                     r[2 * q + 0] = v.x;
                     r[2 * q + 1] = v.y;
                 }
+            }
+            if constexpr (TAIL == 2) {
+                const float2 t = __ldg(tail(sf, V) + (int64_t)plane * V + n);
+                r[16] = t.x;
+                r[17] = t.y;
             }
             Mat<R> u;
 #pragma unroll
@@ -112,8 +128,8 @@ template <typename R, bool FULL> struct Staples {
         if constexpr (!FULL) {
             store_link(sf, V, plane, n, u);
         } else {
-            V4 *p = reinterpret_cast<V4 *>(sf) + (int64_t)plane * LANES * V + n;
-            R r[LANES * W];
+            V4 *p = reinterpret_cast<V4 *>(sf) + (int64_t)plane * NW * V + n;
+            R r[18];
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -122,13 +138,15 @@ template <typename R, bool FULL> struct Staples {
                     r[2 * (3 * i + j) + 1] = u.im[i][j];
                 }
 #pragma unroll
-            for (int e = 18; e < LANES * W; ++e) r[e] = R(0);
-#pragma unroll
-            for (int q = 0; q < LANES; ++q) {
+            for (int q = 0; q < NW; ++q) {
                 V4 v;
                 if constexpr (W == 4) v = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
                 else v = make_double2(r[2 * q], r[2 * q + 1]);
                 p[q * V] = v;
+            }
+            if constexpr (TAIL == 2) {
+                float2 *t = const_cast<float2 *>(tail(sf, V)) + (int64_t)plane * V + n;
+                *t = make_float2(r[16], r[17]);
             }
         }
     }
@@ -673,13 +691,13 @@ cudaError_t launch_sf_batched_t(const ForceArgs &a, int n, const SfLattice *item
 
 } // namespace
 
-// Room for 24 planes in the larger (full) of the two storage forms, so that
-// every schedule fits the same workspace.
+// Room for the 24 planes in the larger (full, 18-real) of the two storage
+// forms, so that every schedule fits the same workspace.
 size_t staple_field_bytes(const int dims[4], int precision)
 {
     const int64_t V = (int64_t)dims[0] * dims[1] * dims[2] * dims[3];
-    const size_t lanes = precision == LQCD_F64 ? Staples<double, true>::LANES : Staples<float, true>::LANES;
-    return ((size_t)24 * lanes * 16 * (size_t)V + 255) & ~(size_t)255;
+    const size_t real = precision == LQCD_F64 ? 8 : 4;
+    return ((size_t)kStaplePlanes * 18 * real * (size_t)V + 255) & ~(size_t)255;
 }
 
 int staple_force_partials(const int dims[4])
