@@ -206,3 +206,70 @@ def test_sampled_full_size(prec):
                                                    int(li) % 4) for li in links])
     assert _rel(d_s, want_d) <= TOL[prec]
     assert _rel(f_l, want_f) <= TOL[prec]
+
+
+def _chiral_gamma5():
+    """gamma_5 = gamma_x gamma_y gamma_z gamma_t of the library's chiral basis
+    (the matrices the header writes out)."""
+    gx = np.array([[0, 0, 0, 1j], [0, 0, 1j, 0], [0, -1j, 0, 0], [-1j, 0, 0, 0]])
+    gy = np.array([[0, 0, 0, -1], [0, 0, 1, 0], [0, 1, 0, 0], [-1, 0, 0, 0]], dtype=complex)
+    gz = np.array([[0, 0, 1j, 0], [0, 0, 0, -1j], [-1j, 0, 0, 0], [0, 1j, 0, 0]])
+    gt = np.array([[0, 0, 1, 0], [0, 0, 0, 1], [1, 0, 0, 0], [0, 1, 0, 0]], dtype=complex)
+    return gx @ gy @ gz @ gt
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 2e-5)])
+def test_gamma5_hermiticity_16x32(prec, tol):
+    """On every site of the 16^3x32 workload: Y^dag calD X = conj(X^dag g5
+    calD g5 Y) (calD^dag = g5 calD g5), with both sides from the GPU."""
+    w = synth.WORKLOADS["16^3x32"]
+    dims = w["dims"]
+    lat = lqcd.Lattice(dims, prec)
+    U = lqcd.links_from_omega(lat, lqcd.algebra_to_device(lat, synth.omega(dims, w["sigma"], 0)))
+    X = _cplx(synth.spinor(dims, 11))
+    Y = _cplx(synth.spinor(dims, 12))
+    g5 = _chiral_gamma5()
+    DX = lqcd.spinor_from_device(lqcd.wilson_dslash(lat, U, lqcd.spinor_to_device(lat, X)))
+    g5Y = np.einsum("ab,nbc->nac", g5, Y)
+    Dg5Y = lqcd.spinor_from_device(lqcd.wilson_dslash(lat, U, lqcd.spinor_to_device(lat, g5Y)))
+    lhs = np.vdot(Y, DX)
+    rhs = np.conj(np.vdot(X, np.einsum("ab,nbc->nac", g5, Dg5Y)))
+    scale = np.sqrt(np.vdot(Y, Y).real * np.vdot(DX, DX).real)
+    assert abs(lhs - rhs) <= tol * scale
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 2e-5)])
+def test_gauge_covariance_16x32(prec, tol):
+    """16^3x32: under U -> g U g^dag (formed in numpy), X -> g X, Y -> g Y,
+    calD X -> g calD X on every site and the force matrix rotates at k."""
+    w = synth.WORKLOADS["16^3x32"]
+    dims = w["dims"]
+    lat = lqcd.Lattice(dims, prec)
+    lat64 = lat.with_(precision="f64")
+    U = lqcd.links_from_omega(lat, lqcd.algebra_to_device(lat, synth.omega(dims, w["sigma"], 0)))
+    full = lqcd.full_from_device(lqcd.unpack_links(lat, U))
+    gl = lqcd.links_from_omega(lat64, lqcd.algebra_to_device(
+        lat64, np.repeat(synth.gauge_parameters(dims, seed=1)[:, None, :], 4, axis=1)))
+    g = lqcd.full_from_device(lqcd.unpack_links(lat64, gl))[:, 0]
+    P = H.site_coords(dims)
+    Ur = np.empty_like(full)
+    for mu in range(4):
+        sh = P.copy()
+        sh[:, mu] = (sh[:, mu] + 1) % dims[mu]
+        nb = sh[:, 0] + dims[0] * (sh[:, 1] + dims[1] * (sh[:, 2] + dims[2] * sh[:, 3]))
+        Ur[:, mu] = g @ full[:, mu] @ np.conj(np.transpose(g[nb], (0, 2, 1)))
+    U2 = lqcd.pack_links(lat, lqcd.full_to_device(lat, Ur))
+    X = _cplx(synth.spinor(dims, 11))
+    Y = _cplx(synth.spinor(dims, 12))
+    gX = np.einsum("nab,nsb->nsa", g, X)
+    gY = np.einsum("nab,nsb->nsa", g, Y)
+    Xd, Yd = lqcd.spinor_to_device(lat, X), lqcd.spinor_to_device(lat, Y)
+    gXd, gYd = lqcd.spinor_to_device(lat, gX), lqcd.spinor_to_device(lat, gY)
+    D1 = lqcd.spinor_from_device(lqcd.wilson_dslash(lat, U, Xd))
+    D2 = lqcd.spinor_from_device(lqcd.wilson_dslash(lat, U2, gXd))
+    assert _rel(D2, np.einsum("nab,nsb->nsa", g, D1)) <= 4 * tol
+    T = H.gell_mann() / 2
+    F1 = np.einsum("nma,aij->nmij", lqcd.algebra_from_device(lqcd.wilson_hopping_force(lat, U, Xd, Yd)), T)
+    F2 = np.einsum("nma,aij->nmij", lqcd.algebra_from_device(lqcd.wilson_hopping_force(lat, U2, gXd, gYd)), T)
+    rot = np.einsum("nij,nmjk,nlk->nmil", g, F1, np.conj(g))
+    assert np.abs(F2 - rot).max() <= 4 * tol * np.abs(F1).max()
