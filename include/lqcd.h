@@ -275,6 +275,18 @@ LQCD_API int lqcd_convert_algebra(const lqcd_desc *desc, const void *src, int ds
 LQCD_API int lqcd_pack_links(const lqcd_desc *desc, const void *full, void *links, void *stream);
 LQCD_API int lqcd_unpack_links(const lqcd_desc *desc, const void *links, void *full, void *stream);
 
+/* Gaussian momenta for the momentum refresh of an HMC trajectory: every
+ * component p^a_{n,mu} ~ N(0, 1), written in the algebra layout (device,
+ * overwritten).  Counter-based, so the field depends only on `seed`:
+ * component a of link (n, mu) is standard normal number j = (n*4 + mu)*8 + a
+ * of the SplitMix64 stream `seed` (Steele, Lea & Flood 2014: word i =
+ * mix(seed + (i+1) * 0x9E3779B97F4A7C15)), by the Box-Muller transform
+ * (cosine branch) of words 2j and 2j+1 taken as the 53-bit uniforms
+ * u1 = ((w >> 11) + 1) * 2^-53 and u2 = (w >> 11) * 2^-53; computed in FP64
+ * and rounded to desc->precision.  Not from the paper (which fixes no HMC
+ * driver).  Errors: LQCD_ERR_ARG, LQCD_ERR_ALIGN, LQCD_ERR_DIMS. */
+LQCD_API int lqcd_gaussian_momenta(const lqcd_desc *desc, uint64_t seed, void *mom, void *stream);
+
 /* ---------------------------------------------- Wilson fermion (Sec. III)
  *
  * Spinor fields hold 4 (Dirac) x 3 (colour) complex numbers per site:

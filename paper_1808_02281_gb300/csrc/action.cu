@@ -8,6 +8,8 @@
 #include <cmath>
 #include <mutex>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kernels.h"
 #include "su3.cuh"
 
@@ -230,6 +232,11 @@ int fixed_partials_address(int device, double **out)
 extern "C" int lqcd_gauge_action_noalloc(const lqcd_desc *desc, const void *links, double *action,
                                          void *stream)
 {
+    // NVTX range named after the entry point (no-op without a profiler)
+    struct Range {
+        Range() { nvtxRangePushA("lqcd_gauge_action_noalloc"); }
+        ~Range() { nvtxRangePop(); }
+    } const trace_range;
     if (desc == nullptr || links == nullptr || action == nullptr) return LQCD_ERR_ARG;
     if (desc->precision != LQCD_F32 && desc->precision != LQCD_F64) return LQCD_ERR_ARG;
     if (!std::isfinite(desc->beta) || !std::isfinite(desc->c_plaq) ||

@@ -4,9 +4,20 @@
 #include <cmath>
 #include <cstdint>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kernels.h"
 
 namespace {
+
+// An NVTX range named after the entry point around every C-ABI call (a
+// no-op unless a profiler is attached), so that traces group each call's
+// kernels under the call that enqueued them.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+};
+#define LQCD_TRACE() const TraceRange lqcd_trace_range_(__func__)
 
 thread_local int g_last_cuda_error = 0;
 
@@ -140,6 +151,7 @@ extern "C" {
 int lqcd_symanzik_coefficients(double u0, double *alpha_s, double *c_plaq, double *c_rect,
                                double *c_cube)
 {
+    LQCD_TRACE();
     if (!std::isfinite(u0) || !(u0 > 0.0)) return LQCD_ERR_ARG;
     const double as = -4.0 * std::log(u0) / 3.06839;
     if (alpha_s) *alpha_s = as;
@@ -151,6 +163,7 @@ int lqcd_symanzik_coefficients(double u0, double *alpha_s, double *c_plaq, doubl
 
 int lqcd_links_from_omega(const lqcd_desc *desc, const void *omega, void *links, void *stream)
 {
+    LQCD_TRACE();
     int s = check_desc(desc);
     if (s) return s;
     if ((s = check_ptrs({omega, links}))) return s;
@@ -166,6 +179,7 @@ int lqcd_links_from_omega(const lqcd_desc *desc, const void *omega, void *links,
 int lqcd_gauge_force(const lqcd_desc *desc, const void *links, void *force, void *workspace,
                      size_t workspace_bytes, void *stream)
 {
+    LQCD_TRACE();
     int s = check_desc(desc);
     if (s) return s;
     if ((s = check_ptrs({links, force}))) return s;
@@ -176,6 +190,7 @@ int lqcd_gauge_force(const lqcd_desc *desc, const void *links, void *force, void
 int lqcd_gauge_force_update_momenta(const lqcd_desc *desc, const void *links, void *mom,
                                     double dt, void *stream)
 {
+    LQCD_TRACE();
     int s = check_desc(desc);
     if (s) return s;
     if ((s = check_ptrs({links, mom}))) return s;
@@ -188,6 +203,7 @@ int lqcd_md_force_step(const lqcd_desc *desc, const void *links, void *force, vo
                        double dt, double *action, void *workspace, size_t workspace_bytes,
                        void *stream)
 {
+    LQCD_TRACE();
     int s = check_desc(desc);
     if (s) return s;
     if ((s = check_ptrs({links}))) return s;
@@ -236,6 +252,7 @@ size_t batch_workspace_bytes(const lqcd_desc *desc, int n, const lqcd_lattice_re
 
 size_t lqcd_workspace_bytes_batched(const lqcd_desc *desc, int n, const lqcd_lattice_ref *lats)
 {
+    LQCD_TRACE();
     if (check_batch(desc, n, lats) != LQCD_OK) return 0;
     return batch_workspace_bytes(desc, n, lats);
 }
@@ -243,6 +260,7 @@ size_t lqcd_workspace_bytes_batched(const lqcd_desc *desc, int n, const lqcd_lat
 int lqcd_md_force_step_batched(const lqcd_desc *desc, int n, const lqcd_lattice_ref *lats,
                                double dt, void *workspace, size_t workspace_bytes, void *stream)
 {
+    LQCD_TRACE();
     int s = check_batch(desc, n, lats);
     if (s) return s;
     if (desc->force_algo != LQCD_FORCE_AUTO && desc->force_algo != LQCD_FORCE_STAPLE_FIELDS)
@@ -286,6 +304,7 @@ int lqcd_md_force_step_batched(const lqcd_desc *desc, int n, const lqcd_lattice_
 int lqcd_md_update_links_batched(const lqcd_desc *desc, int n, const lqcd_lattice_ref *lats,
                                  double dt, void *stream)
 {
+    LQCD_TRACE();
     int s = check_batch(desc, n, lats);
     if (s) return s;
     if (!std::isfinite(dt)) return LQCD_ERR_ARG;
@@ -302,6 +321,7 @@ int lqcd_md_update_links_batched(const lqcd_desc *desc, int n, const lqcd_lattic
 
 int lqcd_force_variant_count(const lqcd_desc *desc)
 {
+    LQCD_TRACE();
     const int s = check_desc(desc);
     if (s) return s;
     const bool sf = desc->force_algo == LQCD_FORCE_AUTO || desc->force_algo == LQCD_FORCE_STAPLE_FIELDS;
@@ -310,6 +330,7 @@ int lqcd_force_variant_count(const lqcd_desc *desc)
 
 int lqcd_get_force_variant(const lqcd_desc *desc)
 {
+    LQCD_TRACE();
     const int s = check_desc(desc);
     if (s) return s;
     const bool sf = desc->force_algo == LQCD_FORCE_AUTO || desc->force_algo == LQCD_FORCE_STAPLE_FIELDS;
@@ -318,6 +339,7 @@ int lqcd_get_force_variant(const lqcd_desc *desc)
 
 int lqcd_set_force_variant(const lqcd_desc *desc, int variant)
 {
+    LQCD_TRACE();
     const int s = check_desc(desc);
     if (s) return s;
     const bool sf = desc->force_algo == LQCD_FORCE_AUTO || desc->force_algo == LQCD_FORCE_STAPLE_FIELDS;
@@ -330,6 +352,7 @@ int lqcd_set_force_variant(const lqcd_desc *desc, int variant)
 int lqcd_autotune_force(const lqcd_desc *desc, const void *links, void *force, void *workspace,
                         size_t workspace_bytes, int reps, void *stream, int *best, float *ms)
 {
+    LQCD_TRACE();
     int s = check_desc(desc);
     if (s) return s;
     if ((s = check_ptrs({links, force}))) return s;
@@ -384,6 +407,7 @@ int lqcd_autotune_force(const lqcd_desc *desc, const void *links, void *force, v
 int lqcd_gauge_action(const lqcd_desc *desc, const void *links, double *action, void *workspace,
                       size_t workspace_bytes, void *stream)
 {
+    LQCD_TRACE();
     int s = check_desc(desc);
     if (s) return s;
     if ((s = check_ptrs({links}))) return s;
@@ -408,6 +432,7 @@ int lqcd_gauge_action(const lqcd_desc *desc, const void *links, double *action, 
 int lqcd_kinetic_energy(const lqcd_desc *desc, const void *mom, double *energy, void *workspace,
                         size_t workspace_bytes, void *stream)
 {
+    LQCD_TRACE();
     int s = check_desc(desc);
     if (s) return s;
     if ((s = check_ptrs({mom}))) return s;
@@ -428,6 +453,7 @@ int lqcd_kinetic_energy(const lqcd_desc *desc, const void *mom, double *energy, 
 int lqcd_md_update_momenta(const lqcd_desc *desc, void *mom, const void *force, double dt,
                            void *stream)
 {
+    LQCD_TRACE();
     int s = check_desc(desc);
     if (s) return s;
     if ((s = check_ptrs({mom, force}))) return s;
@@ -444,6 +470,7 @@ int lqcd_md_update_momenta(const lqcd_desc *desc, void *mom, const void *force, 
 int lqcd_md_update_links(const lqcd_desc *desc, void *links, const void *mom, double dt,
                          void *stream)
 {
+    LQCD_TRACE();
     int s = check_desc(desc);
     if (s) return s;
     if ((s = check_ptrs({links, mom}))) return s;
@@ -460,6 +487,7 @@ int lqcd_md_update_links(const lqcd_desc *desc, void *links, const void *mom, do
 int lqcd_omega_gradient(const lqcd_desc *desc, const void *omega, const void *force, void *grad,
                         void *stream)
 {
+    LQCD_TRACE();
     int s = check_desc(desc);
     if (s) return s;
     if ((s = check_ptrs({omega, force, grad}))) return s;
@@ -473,9 +501,24 @@ int lqcd_omega_gradient(const lqcd_desc *desc, const void *omega, const void *fo
     return cuda_status(lqcd::launch_omega_gradient(a, as_stream(stream)));
 }
 
+int lqcd_gaussian_momenta(const lqcd_desc *desc, uint64_t seed, void *mom, void *stream)
+{
+    LQCD_TRACE();
+    int s = check_desc(desc);
+    if (s) return s;
+    if ((s = check_ptrs({mom}))) return s;
+    lqcd::MdArgs a{};
+    copy_dims(a.dims, desc);
+    a.precision = desc->precision;
+    a.mom_out = mom;
+    a.seed = seed;
+    return cuda_status(lqcd::launch_gaussian_momenta(a, as_stream(stream)));
+}
+
 int lqcd_wilson_dslash(const lqcd_desc *desc, const void *links, const void *x, double a, double b,
                        void *y, void *stream)
 {
+    LQCD_TRACE();
     int s = check_desc(desc);
     if (s) return s;
     if ((s = check_ptrs({links, x, y}))) return s;
@@ -494,6 +537,7 @@ int lqcd_wilson_dslash(const lqcd_desc *desc, const void *links, const void *x, 
 int lqcd_wilson_hopping_force(const lqcd_desc *desc, const void *links, const void *X, const void *Y,
                               double coef, void *force, void *mom, double dt, void *stream)
 {
+    LQCD_TRACE();
     int s = check_desc(desc);
     if (s) return s;
     if ((s = check_ptrs({links, X, Y}))) return s;
@@ -520,6 +564,7 @@ int lqcd_wilson_hopping_force(const lqcd_desc *desc, const void *links, const vo
 int lqcd_measure_fma_rate(int precision, void *scratch, size_t scratch_bytes, double *tflops,
                           void *stream)
 {
+    LQCD_TRACE();
     if ((precision != LQCD_F32 && precision != LQCD_F64) || tflops == nullptr) return LQCD_ERR_ARG;
     if (scratch == nullptr || scratch_bytes < lqcd::fma_rate_scratch_bytes() || !aligned16(scratch))
         return LQCD_ERR_WORKSPACE;
@@ -532,6 +577,7 @@ size_t lqcd_fma_rate_scratch_bytes(void) { return lqcd::fma_rate_scratch_bytes()
 static int convert_common(const lqcd_desc *desc, const void *src, int dst_precision, void *dst,
                           bool links, void *stream)
 {
+    LQCD_TRACE();
     int s = check_desc(desc);
     if (s) return s;
     if ((s = check_ptrs({src, dst}))) return s;
@@ -548,17 +594,20 @@ static int convert_common(const lqcd_desc *desc, const void *src, int dst_precis
 int lqcd_convert_links(const lqcd_desc *desc, const void *src, int dst_precision, void *dst,
                        void *stream)
 {
+    LQCD_TRACE();
     return convert_common(desc, src, dst_precision, dst, true, stream);
 }
 
 int lqcd_convert_algebra(const lqcd_desc *desc, const void *src, int dst_precision, void *dst,
                          void *stream)
 {
+    LQCD_TRACE();
     return convert_common(desc, src, dst_precision, dst, false, stream);
 }
 
 int lqcd_pack_links(const lqcd_desc *desc, const void *full, void *links, void *stream)
 {
+    LQCD_TRACE();
     int s = check_desc(desc);
     if (s) return s;
     if ((s = check_ptrs({full, links}))) return s;
@@ -573,6 +622,7 @@ int lqcd_pack_links(const lqcd_desc *desc, const void *full, void *links, void *
 
 int lqcd_unpack_links(const lqcd_desc *desc, const void *links, void *full, void *stream)
 {
+    LQCD_TRACE();
     int s = check_desc(desc);
     if (s) return s;
     if ((s = check_ptrs({full, links}))) return s;
@@ -587,6 +637,7 @@ int lqcd_unpack_links(const lqcd_desc *desc, const void *links, void *full, void
 
 size_t lqcd_workspace_bytes(const lqcd_desc *desc)
 {
+    LQCD_TRACE();
     if (check_desc(desc) != LQCD_OK) return 0;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;

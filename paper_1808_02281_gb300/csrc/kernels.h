@@ -134,6 +134,7 @@ struct MdArgs {
     const void *full_in;
     void *full_out;
     double dt;
+    uint64_t seed; // gaussian momenta: the generator stream
 };
 
 cudaError_t launch_update_momenta(const MdArgs &a, cudaStream_t st);
@@ -152,6 +153,8 @@ cudaError_t launch_omega_gradient(const MdArgs &a, cudaStream_t st);
 cudaError_t launch_convert(const MdArgs &a, int dst_precision, bool links, cudaStream_t st);
 cudaError_t launch_pack(const MdArgs &a, cudaStream_t st);
 cudaError_t launch_unpack(const MdArgs &a, cudaStream_t st);
+// mom_out <- Gaussian momenta of stream a.seed (SplitMix64 + Box-Muller).
+cudaError_t launch_gaussian_momenta(const MdArgs &a, cudaStream_t st);
 
 // Wilson fermion hopping term (Sec. III).  Spinor fields: 24 reals per site,
 // real r = 2*(3*alpha + a) + (0 re, 1 im) of site n at ((r/W)*V + n)*W + r%W.

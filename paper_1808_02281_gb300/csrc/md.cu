@@ -281,7 +281,55 @@ __global__ void __launch_bounds__(kBlock) unpack(const R *__restrict__ links, R 
     }
 }
 
+// Word i of the counter-based SplitMix64 stream `seed` (Steele, Lea & Flood,
+// "Fast splittable pseudorandom number generators", OOPSLA 2014):
+// mix(seed + (i + 1) * golden gamma) with the published finaliser.
+__device__ __forceinline__ uint64_t splitmix_word(uint64_t seed, uint64_t i)
+{
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Standard normal j of stream `seed`: the Box-Muller transform (cosine
+// branch) of words 2j and 2j+1 as 53-bit uniforms, u1 in (0, 1], u2 in [0, 1).
+__device__ __forceinline__ double gaussian_of(uint64_t seed, uint64_t j)
+{
+    const uint64_t w1 = splitmix_word(seed, 2 * j), w2 = splitmix_word(seed, 2 * j + 1);
+    const double u1 = ((double)(w1 >> 11) + 1.0) * 0x1p-53;
+    const double u2 = (double)(w2 >> 11) * 0x1p-53;
+    return sqrt(-2.0 * log(u1)) * cos(2.0 * 3.141592653589793 * u2);
+}
+
+// p^a_{n,mu} = normal number (n*4 + mu)*8 + a of the stream, in FP64,
+// rounded to the storage precision.
+template <typename R>
+__global__ void __launch_bounds__(kBlock) gaussian_momenta(R *__restrict__ mom, int64_t V, uint64_t seed)
+{
+    const int64_t nlinks = 4 * V;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nlinks;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int mu = (int)(i / V);
+        const int64_t n = i - mu * V;
+        R p[8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) p[a] = (R)gaussian_of(seed, (uint64_t)((n * 4 + mu) * 8 + a));
+        store_algebra(mom, V, mu, n, p);
+    }
+}
+
 } // namespace
+
+cudaError_t launch_gaussian_momenta(const MdArgs &a, cudaStream_t st)
+{
+    const int64_t V = volume(a.dims);
+    if (a.precision == LQCD_F64)
+        gaussian_momenta<double><<<grid_for(4 * V), kBlock, 0, st>>>(static_cast<double *>(a.mom_out), V, a.seed);
+    else
+        gaussian_momenta<float><<<grid_for(4 * V), kBlock, 0, st>>>(static_cast<float *>(a.mom_out), V, a.seed);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_update_momenta(const MdArgs &a, cudaStream_t st)
 {

@@ -14,13 +14,24 @@ momenta, S from the action kernel, for FP32-stored links either in FP32
 arithmetic or (``action_precision="f64"``) in FP64 arithmetic on the same
 stored values.  A whole trajectory can be captured as one CUDA graph.
 
-``python -m paper_1808_02281_gb300.hmc`` runs the dH-versus-dt study.
+A full HMC run (``run_hmc``) adds to each trajectory the momentum refresh
+(Gaussian momenta drawn on the GPU from a counter-based stream), the
+Metropolis test accept with probability min(1, exp(-dH)) (the links are
+restored on rejection) and a record per trajectory (dH, acceptance, action,
+plaquette); ``save_checkpoint`` / ``load_checkpoint`` store and restore the
+state so that a resumed run continues bit for bit.
+
+``python -m paper_1808_02281_gb300.hmc`` runs the dH-versus-dt study;
+``--hmc N`` runs N HMC trajectories instead (JSON line per trajectory).
 """
 from __future__ import annotations
 
 import argparse
 import dataclasses
 import json
+import math
+import os
+import struct
 import time
 
 import torch
@@ -235,6 +246,146 @@ def dh_study(dims, tau: float, dts, integrator: str, precisions, seed: int = 0):
             torch.cuda.empty_cache()
 
 
+# ------------------------------------------------------------- HMC runs
+
+def plaquette(st: MDState) -> float:
+    """Average Re tr P / 3 over the 6V plaquettes, from the action kernel
+    with Wilson coefficients: S_W = (beta/3) sum (3 - Re tr P)."""
+    lat = st.lat.with_(c_plaq=1.0, c_rect=0.0, c_cube=0.0)
+    S_w = float(lqcd.gauge_action(lat, st.links, workspace=st.workspace).item())
+    return 1.0 - S_w / (6.0 * lat.beta * lat.V)
+
+
+@dataclasses.dataclass
+class HMCConfig:
+    tau: float = 1.0
+    dt: float = 0.05
+    integrator: str = "omelyan"
+    seed: int = 1
+    action_precision: str | None = None   # "f64" for FP32 runs: Metropolis on the FP64 action
+
+
+def _stream_word(seed: int, i: int) -> int:
+    return int(synth.words(seed, i, 1)[0])
+
+
+def momentum_seed(cfg: HMCConfig, trajectory: int) -> int:
+    """Generator stream of the momenta of trajectory t: word t of stream seed."""
+    return _stream_word(cfg.seed, trajectory)
+
+
+def metropolis_uniform(cfg: HMCConfig, trajectory: int) -> float:
+    """Uniform in [0, 1) of trajectory t: word t of stream seed + 1, top 53 bits."""
+    return (_stream_word(cfg.seed + 1, trajectory) >> 11) * 2.0 ** -53
+
+
+def hmc_trajectory(st: MDState, cfg: HMCConfig, trajectory: int) -> dict:
+    """One HMC trajectory in place: refresh, integrate, Metropolis test."""
+    t0 = time.perf_counter()
+    lqcd.gaussian_momenta(st.lat, momentum_seed(cfg, trajectory), out=st.mom)
+    saved = st.links.clone()
+    nsteps = max(1, int(round(cfg.tau / cfg.dt)))
+    H0 = hamiltonian(st, cfg.action_precision)
+    INTEGRATORS[cfg.integrator](st, cfg.tau / nsteps, nsteps)
+    H1 = hamiltonian(st, cfg.action_precision)
+    dH = H1 - H0
+    accept = metropolis_uniform(cfg, trajectory) < math.exp(min(0.0, -dH))
+    if not accept:
+        st.links.copy_(saved)
+    del saved
+    S = float(lqcd.gauge_action(st.lat, st.links, workspace=st.workspace).item())
+    return {"trajectory": trajectory, "dH": dH, "accepted": bool(accept), "action": S,
+            "plaquette": plaquette(st), "nsteps": nsteps,
+            "forces": force_evaluations(cfg.integrator, nsteps),
+            "seconds": time.perf_counter() - t0}
+
+
+def run_hmc(st: MDState, cfg: HMCConfig, n: int, start: int = 0, checkpoint: str | None = None,
+            every: int = 0):
+    """Trajectories start .. start+n-1 (yields one record each); with a
+    checkpoint path, the state is saved after every `every` trajectories
+    (and after the last)."""
+    accepted = 0
+    for i in range(n):
+        t = start + i
+        rec = hmc_trajectory(st, cfg, t)
+        accepted += rec["accepted"]
+        rec["acceptance"] = accepted / (i + 1)
+        if checkpoint and ((every and (i + 1) % every == 0) or i == n - 1):
+            save_checkpoint(checkpoint, st, cfg, next_trajectory=t + 1)
+        yield rec
+
+
+# ----------------------------------------------------------- checkpoints
+
+_MAGIC = b"LQCDCKPT"
+_VERSION = 1
+
+
+def save_fields(path: str, meta: dict, fields: dict) -> None:
+    """Binary checkpoint: magic, version, header length, a JSON header (meta
+    and, per tensor, name, shape, dtype, byte offset and length), then the
+    raw tensor bytes.  Written to a temporary file and renamed."""
+    entries, blobs, off = [], [], 0
+    for name, t in fields.items():
+        a = t.detach().to("cpu").contiguous()
+        b = a.numpy().tobytes()
+        entries.append({"name": name, "shape": list(a.shape), "dtype": str(a.dtype).split(".")[-1],
+                        "offset": off, "nbytes": len(b)})
+        blobs.append(b)
+        off += len(b)
+    header = json.dumps({"meta": meta, "tensors": entries}).encode()
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "wb") as fh:
+        fh.write(_MAGIC + struct.pack("<II", _VERSION, len(header)) + header)
+        for b in blobs:
+            fh.write(b)
+    os.replace(tmp, path)
+
+
+def load_fields(path: str, device="cpu"):
+    """(meta, {name: tensor}) from a file written by save_fields."""
+    with open(path, "rb") as fh:
+        data = fh.read()
+    if data[:8] != _MAGIC:
+        raise ValueError(f"{path}: not a checkpoint")
+    version, hlen = struct.unpack("<II", data[8:16])
+    if version != _VERSION:
+        raise ValueError(f"{path}: checkpoint version {version}, expected {_VERSION}")
+    header = json.loads(data[16:16 + hlen])
+    base = 16 + hlen
+    out = {}
+    for e in header["tensors"]:
+        lo = base + e["offset"]
+        if lo + e["nbytes"] > len(data):
+            raise ValueError(f"{path}: truncated at tensor {e['name']}")
+        dtype = getattr(torch, e["dtype"])
+        t = torch.frombuffer(bytearray(data[lo:lo + e["nbytes"]]), dtype=dtype).reshape(e["shape"])
+        out[e["name"]] = t.to(device)
+    return header["meta"], out
+
+
+def save_checkpoint(path: str, st: MDState, cfg: HMCConfig | None = None,
+                    next_trajectory: int = 0) -> None:
+    """Links, momenta, lattice parameters, HMC settings and the index of the
+    next trajectory (which fixes the generator streams of the rest of the run)."""
+    lat = st.lat
+    meta = {"dims": list(lat.dims), "precision": lat.precision, "beta": lat.beta,
+            "c_plaq": lat.c_plaq, "c_rect": lat.c_rect, "c_cube": lat.c_cube,
+            "force_algo": lat.force_algo, "next_trajectory": next_trajectory,
+            "hmc": dataclasses.asdict(cfg) if cfg is not None else None}
+    save_fields(path, meta, {"links": st.links, "mom": st.mom})
+
+
+def load_checkpoint(path: str, device="cuda"):
+    """(MDState, HMCConfig or None, next trajectory) from save_checkpoint's file."""
+    meta, f = load_fields(path, device)
+    lat = lqcd.Lattice(tuple(meta["dims"]), meta["precision"], meta["beta"], meta["c_plaq"],
+                       meta["c_rect"], meta["c_cube"], meta["force_algo"])
+    cfg = HMCConfig(**meta["hmc"]) if meta.get("hmc") else None
+    return MDState.create(lat, f["links"], f["mom"]), cfg, meta["next_trajectory"]
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description="dH against dt for FP32 and FP64 trajectories")
     ap.add_argument("--dims", type=int, nargs=4, default=[48, 48, 48, 96])
@@ -243,9 +394,25 @@ def main(argv=None):
     ap.add_argument("--integrator", choices=sorted(INTEGRATORS), default="omelyan")
     ap.add_argument("--precisions", nargs="+", default=["f32", "f64"])
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--hmc", type=int, default=0, metavar="N",
+                    help="run N HMC trajectories (first precision, first dt) instead of the study")
+    ap.add_argument("--checkpoint", default=None, help="HMC: checkpoint file (resumed if present)")
     args = ap.parse_args(argv)
     from . import build
     build.build()
+    if args.hmc:
+        prec = args.precisions[0]
+        cfg = HMCConfig(tau=args.tau, dt=args.dts[0], integrator=args.integrator,
+                        seed=args.seed + 1, action_precision="f64" if prec == "f32" else None)
+        start = 0
+        if args.checkpoint and os.path.exists(args.checkpoint):
+            st, saved_cfg, start = load_checkpoint(args.checkpoint)
+            cfg = saved_cfg or cfg
+        else:
+            st = initial_state(tuple(args.dims), prec, seed=args.seed)
+        for rec in run_hmc(st, cfg, args.hmc, start=start, checkpoint=args.checkpoint, every=1):
+            print(json.dumps(rec), flush=True)
+        return
     for rec in dh_study(tuple(args.dims), args.tau, args.dts, args.integrator, args.precisions,
                         args.seed):
         print(json.dumps(rec), flush=True)

@@ -87,6 +87,8 @@ _EXPORTS = {
     "lqcd_wilson_hopping_force": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
                                                  ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]),
+    "lqcd_gaussian_momenta": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_uint64, ctypes.c_void_p,
+                                             ctypes.c_void_p]),
     "lqcd_measure_fma_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
                                              ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "lqcd_fma_rate_scratch_bytes": (ctypes.c_size_t, []),
@@ -267,6 +269,18 @@ def wilson_hopping_force(lat: Lattice, links: torch.Tensor, X: torch.Tensor, Y: 
     return force
 
 
+def gaussian_momenta(lat: Lattice, seed: int, out: torch.Tensor | None = None,
+                     device=None, stream=None) -> torch.Tensor:
+    """p^a ~ N(0, 1) on every link from the counter-based stream `seed`
+    (the same numbers as synth.momenta(dims, seed), drawn on the GPU)."""
+    out = empty_algebra(lat, device) if out is None else out
+    _check(out, lat, lat.algebra_shape, "mom")
+    d = lat.desc()
+    _call("lqcd_gaussian_momenta", ctypes.byref(d), ctypes.c_uint64(int(seed) & (2**64 - 1)),
+          _ptr(out), _stream(stream))
+    return out
+
+
 def measure_fma_rate(precision: str = "f32", device=None, stream=None) -> float:
     """FMA issue rate of the device in TFLOP/s (FP32 or FP64; ~20 ms,
     synchronises)."""
@@ -410,22 +424,27 @@ def omega_gradient(lat: Lattice, omega: torch.Tensor, force: torch.Tensor,
     return out
 
 
-def convert_links(lat: Lattice, links: torch.Tensor, precision: str, stream=None) -> torch.Tensor:
-    """The same links stored in another precision (new tensor)."""
+def convert_links(lat: Lattice, links: torch.Tensor, precision: str,
+                  out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """The same links stored in another precision (into `out` or a new tensor)."""
     _check(links, lat, lat.link_shape, "links")
     dst_lat = lat.with_(precision=precision)
-    out = empty_links(dst_lat, links.device)
+    out = empty_links(dst_lat, links.device) if out is None else out
+    _check(out, dst_lat, dst_lat.link_shape, "out")
     d = lat.desc()
     _call("lqcd_convert_links", ctypes.byref(d), _ptr(links), F32 if precision == "f32" else F64,
           _ptr(out), _stream(stream))
     return out
 
 
-def convert_algebra(lat: Lattice, field: torch.Tensor, precision: str, stream=None) -> torch.Tensor:
-    """The same algebra field (momenta, force) in another precision."""
+def convert_algebra(lat: Lattice, field: torch.Tensor, precision: str,
+                    out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """The same algebra field (momenta, force) in another precision (into
+    `out` or a new tensor)."""
     _check(field, lat, lat.algebra_shape, "field")
     dst_lat = lat.with_(precision=precision)
-    out = empty_algebra(dst_lat, field.device)
+    out = empty_algebra(dst_lat, field.device) if out is None else out
+    _check(out, dst_lat, dst_lat.algebra_shape, "out")
     d = lat.desc()
     _call("lqcd_convert_algebra", ctypes.byref(d), _ptr(field), F32 if precision == "f32" else F64,
           _ptr(out), _stream(stream))

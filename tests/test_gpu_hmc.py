@@ -107,3 +107,62 @@ def test_convert_roundtrip():
     p = lqcd.algebra_to_device(lat, synth.momenta(DIMS, 3))
     p64 = lqcd.convert_algebra(lat, p, "f64")
     np.testing.assert_array_equal(lqcd.algebra_from_device(p64), lqcd.algebra_from_device(p))
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-13), ("f32", 1e-6)])
+def test_gaussian_momenta_match_the_generator(prec, tol):
+    """The GPU draws are the generator's: synth.momenta(dims, seed), the same
+    SplitMix64 + Box-Muller definition evaluated in numpy (libm ulps apart)."""
+    dims = (3, 5, 4, 6)
+    lat = lqcd.Lattice(dims, prec)
+    for seed in (0, 12345, 2**63 + 11):
+        got = lqcd.algebra_from_device(lqcd.gaussian_momenta(lat, seed))
+        want = synth.momenta(dims, seed % 2**64)
+        assert np.abs(got - want).max() <= tol * max(1.0, np.abs(want).max())
+    big = lqcd.algebra_from_device(lqcd.gaussian_momenta(lqcd.Lattice((16, 16, 16, 32), prec), 7))
+    assert abs(big.mean()) < 3e-3 and abs(big.var() - 1.0) < 3e-3
+
+
+def test_plaquette_against_oracle():
+    st = _state("f64")
+    U = O.links_from_omega(synth.omega(DIMS, 0.5, 0))
+    sums = O.loop_sums(DIMS, U)
+    want = 1.0 - sums[0] / (18.0 * 256)
+    assert abs(hmc.plaquette(st) - want) < 1e-13
+    unit = hmc.initial_state(DIMS, "f64", sigma=0.0)
+    assert hmc.plaquette(unit) == 1.0
+
+
+def test_metropolis_branches(monkeypatch):
+    """Rejection restores the links bit for bit; acceptance keeps the
+    integrated ones; the momenta are refreshed from the trajectory's stream."""
+    cfg = hmc.HMCConfig(tau=0.2, dt=0.05, integrator="leapfrog", seed=9)
+    st = _state("f64")
+    U0 = st.links.clone()
+    monkeypatch.setattr(hmc, "metropolis_uniform", lambda cfg, t: 1.0)
+    rec = hmc.hmc_trajectory(st, cfg, 0)
+    assert not rec["accepted"] and torch.equal(st.links, U0)
+    monkeypatch.setattr(hmc, "metropolis_uniform", lambda cfg, t: 0.0)
+    rec = hmc.hmc_trajectory(st, cfg, 0)
+    assert rec["accepted"] and not torch.equal(st.links, U0)
+    # the trajectory started from the refreshed momenta of stream word 0
+    st2 = _state("f64")
+    lqcd.gaussian_momenta(st2.lat, hmc.momentum_seed(cfg, 0), out=st2.mom)
+    hmc.leapfrog(st2, 0.05, 4)
+    assert torch.equal(st2.links, st.links)
+
+
+def test_resume_from_checkpoint_is_bitwise(tmp_path):
+    cfg = hmc.HMCConfig(tau=0.2, dt=0.05, integrator="omelyan", seed=3)
+    st = _state("f64")
+    full = list(hmc.run_hmc(st, cfg, 4))
+    path = str(tmp_path / "run.ckpt")
+    st2 = _state("f64")
+    first = list(hmc.run_hmc(st2, cfg, 2, checkpoint=path))
+    st3, cfg3, start = hmc.load_checkpoint(path)
+    assert start == 2 and cfg3 == cfg
+    rest = list(hmc.run_hmc(st3, cfg3, 2, start=start))
+    assert torch.equal(st3.links, st.links) and torch.equal(st3.mom, st.mom)
+    for a, b in zip(full, first + rest):
+        assert a["dH"] == b["dH"] and a["accepted"] == b["accepted"] and a["action"] == b["action"]
+    assert sum(r["accepted"] for r in full) >= 3    # small dt: nearly every trajectory accepted
