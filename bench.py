@@ -558,9 +558,9 @@ def run_ours(args):
     streaming["md_update_links"]["frac"] = streaming["md_update_links"]["gbs"] / hbm_peak
     cpu = None
     if world == 1 or rank == 0:
-        rate, secs = oracle_step_rate(steps=3)
+        rate, secs = oracle_step_rate(steps=5)
         cpu = {"value": rate / 1e9, "unit": "Glink/s", "cores": 1, "kind": "oracle",
-               "sample": f"3 oracle steps (force, momentum step, link step, action) of a "
+               "sample": f"5 oracle steps (force, momentum step, link step, action) of a "
                          f"{'x'.join(map(str, CPU_SAMPLE_DIMS))} lattice drawn like the "
                          f"{WORKLOAD} workload, single-threaded, {secs:.1f} s"}
     out = {
