@@ -13,6 +13,7 @@ Everything follows D. Li, "The Calculation of Force in Lattice QCD", Sec. II
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -42,41 +43,68 @@ def build(force: bool = False) -> str:
 _lib = None
 
 
+def build_variant(source: str, path: str) -> str:
+    """Compile C source text (a copy of the oracle) to `path` with the same
+    flags as build(); used by the tests that plant mistakes in a copy."""
+    src = path + ".c"
+    with open(src, "w") as fh:
+        fh.write(source)
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", path, src, "-lm"],
+                   check=True)
+    return path
+
+
+def _bind(L):
+    L.oracle_coefficients.argtypes = [ctypes.c_double, _dbl_p]
+    L.oracle_paths.argtypes = [_int_p, _int_p, _int_p]
+    L.oracle_paths.restype = ctypes.c_int
+    L.oracle_loop_sums.argtypes = [_int_p, _dbl_p, _dbl_p]
+    L.oracle_gauge_action.argtypes = [_int_p, _dbl_p, ctypes.c_double, _dbl_p]
+    L.oracle_gauge_action.restype = ctypes.c_double
+    L.oracle_gauge_action_local.argtypes = [
+        _int_p, _dbl_p, ctypes.c_double, _dbl_p, ctypes.c_long, ctypes.c_int]
+    L.oracle_gauge_action_local.restype = ctypes.c_double
+    L.oracle_gauge_force.argtypes = [_int_p, _dbl_p, ctypes.c_double, _dbl_p, _dbl_p]
+    L.oracle_gauge_force_link.argtypes = [
+        _int_p, _dbl_p, ctypes.c_double, _dbl_p, ctypes.c_long, ctypes.c_int, _dbl_p]
+    L.oracle_exp_i_algebra.argtypes = [_dbl_p, _dbl_p]
+    L.oracle_links_from_omega.argtypes = [ctypes.c_long, _dbl_p, _dbl_p]
+    L.oracle_md_update_momenta.argtypes = [ctypes.c_long, _dbl_p, _dbl_p, ctypes.c_double]
+    L.oracle_md_update_links.argtypes = [ctypes.c_long, _dbl_p, _dbl_p, ctypes.c_double]
+    L.oracle_kinetic_energy.argtypes = [ctypes.c_long, _dbl_p]
+    L.oracle_kinetic_energy.restype = ctypes.c_double
+    L.oracle_gauge_transform.argtypes = [_int_p, _dbl_p, _dbl_p, _dbl_p]
+    L.oracle_algebra_to_matrix.argtypes = [_dbl_p, _dbl_p]
+    L.oracle_traceless_antihermitian.argtypes = [_dbl_p, _dbl_p]
+    L.oracle_generator.argtypes = [ctypes.c_int, _dbl_p]
+    L.oracle_gamma.argtypes = [ctypes.c_int, _dbl_p]
+    L.oracle_wilson_hopping.argtypes = [_int_p, _dbl_p, _dbl_p, _dbl_p]
+    L.oracle_wilson_hopping_site.argtypes = [_int_p, _dbl_p, _dbl_p, ctypes.c_long, _dbl_p]
+    L.oracle_wilson_hopping_force.argtypes = [_int_p, _dbl_p, _dbl_p, _dbl_p, ctypes.c_double,
+                                              _dbl_p]
+    L.oracle_wilson_hopping_force_link.argtypes = [
+        _int_p, _dbl_p, _dbl_p, _dbl_p, ctypes.c_double, ctypes.c_long, ctypes.c_int, _dbl_p]
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
-        L = _lib
-        L.oracle_coefficients.argtypes = [ctypes.c_double, _dbl_p]
-        L.oracle_paths.argtypes = [_int_p, _int_p, _int_p]
-        L.oracle_paths.restype = ctypes.c_int
-        L.oracle_loop_sums.argtypes = [_int_p, _dbl_p, _dbl_p]
-        L.oracle_gauge_action.argtypes = [_int_p, _dbl_p, ctypes.c_double, _dbl_p]
-        L.oracle_gauge_action.restype = ctypes.c_double
-        L.oracle_gauge_action_local.argtypes = [
-            _int_p, _dbl_p, ctypes.c_double, _dbl_p, ctypes.c_long, ctypes.c_int]
-        L.oracle_gauge_action_local.restype = ctypes.c_double
-        L.oracle_gauge_force.argtypes = [_int_p, _dbl_p, ctypes.c_double, _dbl_p, _dbl_p]
-        L.oracle_gauge_force_link.argtypes = [
-            _int_p, _dbl_p, ctypes.c_double, _dbl_p, ctypes.c_long, ctypes.c_int, _dbl_p]
-        L.oracle_exp_i_algebra.argtypes = [_dbl_p, _dbl_p]
-        L.oracle_links_from_omega.argtypes = [ctypes.c_long, _dbl_p, _dbl_p]
-        L.oracle_md_update_momenta.argtypes = [ctypes.c_long, _dbl_p, _dbl_p, ctypes.c_double]
-        L.oracle_md_update_links.argtypes = [ctypes.c_long, _dbl_p, _dbl_p, ctypes.c_double]
-        L.oracle_kinetic_energy.argtypes = [ctypes.c_long, _dbl_p]
-        L.oracle_kinetic_energy.restype = ctypes.c_double
-        L.oracle_gauge_transform.argtypes = [_int_p, _dbl_p, _dbl_p, _dbl_p]
-        L.oracle_algebra_to_matrix.argtypes = [_dbl_p, _dbl_p]
-        L.oracle_traceless_antihermitian.argtypes = [_dbl_p, _dbl_p]
-        L.oracle_generator.argtypes = [ctypes.c_int, _dbl_p]
-        L.oracle_gamma.argtypes = [ctypes.c_int, _dbl_p]
-        L.oracle_wilson_hopping.argtypes = [_int_p, _dbl_p, _dbl_p, _dbl_p]
-        L.oracle_wilson_hopping_site.argtypes = [_int_p, _dbl_p, _dbl_p, ctypes.c_long, _dbl_p]
-        L.oracle_wilson_hopping_force.argtypes = [_int_p, _dbl_p, _dbl_p, _dbl_p, ctypes.c_double,
-                                                  _dbl_p]
-        L.oracle_wilson_hopping_force_link.argtypes = [
-            _int_p, _dbl_p, _dbl_p, _dbl_p, ctypes.c_double, ctypes.c_long, ctypes.c_int, _dbl_p]
+        _lib = _bind(ctypes.CDLL(build()))
     return _lib
+
+
+@contextlib.contextmanager
+def using_library(path: str):
+    """Route every oracle call through another build of the oracle for the
+    duration of the block (the tests that plant mistakes use it)."""
+    global _lib
+    saved = lib()
+    _lib = _bind(ctypes.CDLL(path))
+    try:
+        yield
+    finally:
+        _lib = saved
 
 
 def _d(a: np.ndarray):
