@@ -71,6 +71,8 @@ template <typename R> __device__ __forceinline__ R scalar(const KernelScalars &s
 // lane q at ((P*NW + q)*V + n); in FP32 the last two reals of every plane go
 // to a float2 region after all 24*4 lanes, at (P*V + n): 72 bytes per staple
 // instead of 80, with every load and store still 16- or 8-byte aligned.
+// Pass A writes them with evict-first stores: the 3.6 GB (at 32^3x64) would
+// otherwise push the links that pass A re-reads out of L2.
 constexpr int kStaplePlanes = 24;
 
 template <typename R, bool FULL> struct Staples {
@@ -78,6 +80,7 @@ template <typename R, bool FULL> struct Staples {
     static constexpr int W = Vec<R>::W;
     static constexpr int NW = FULL ? 18 / W : 12 / W; // whole lanes per plane
     static constexpr int TAIL = FULL ? 18 - NW * W : 0; // reals in the float2 region (FP32 full: 2)
+    static_assert(NW * W + TAIL == (FULL ? 18 : 12), "a plane holds 12 (compact) or 18 reals");
 
     static __device__ __forceinline__ const float2 *tail(const R *sf, int64_t V)
     {
@@ -142,11 +145,11 @@ template <typename R, bool FULL> struct Staples {
                 V4 v;
                 if constexpr (W == 4) v = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
                 else v = make_double2(r[2 * q], r[2 * q + 1]);
-                p[q * V] = v;
+                __stcs(p + q * V, v);
             }
             if constexpr (TAIL == 2) {
                 float2 *t = const_cast<float2 *>(tail(sf, V)) + (int64_t)plane * V + n;
-                *t = make_float2(r[16], r[17]);
+                __stcs(t, make_float2(r[16], r[17]));
             }
         }
     }
