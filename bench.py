@@ -20,6 +20,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import multiprocessing
 import os
 import re
 import statistics
@@ -173,30 +174,69 @@ def oracle_step_rate(dims=CPU_SAMPLE_DIMS, steps: int = 1):
     return 4 * synth.volume(dims) * steps / dt, dt
 
 
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def _oracle_replica(steps: int):
+    """One worker of the all-cores oracle timing (a separate process)."""
+    rate, secs = oracle_step_rate(steps=steps)
+    return rate, secs
+
+
+class OracleReplicas:
+    """The oracle as it stands, one independent replica per host core: a
+    process pool started with spawn (never forked from a process that holds
+    a CUDA context); throughput = the sum of the replicas' rates."""
+
+    def __init__(self, workers: int | None = None):
+        from oracle import oracle as O
+        O.build()                      # compiled once, before the workers load it
+        self.workers = workers or host_cores()
+        self.pool = multiprocessing.get_context("spawn").Pool(self.workers)
+
+    def step(self, steps: int = 1):
+        """(aggregate links/s, wall seconds) of `steps` oracle steps on every core."""
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_replica, [steps] * self.workers)
+        return sum(r for r, _ in res), time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    for _ in range(args.warmup):
-        oracle_step_rate(steps=1)
-    rates, secs = [], []
-    for _ in range(args.steps):
-        r, s = oracle_step_rate(steps=1)
-        rates.append(r)
-        secs.append(s)
-    total_links = 4 * int(np.prod(CPU_SAMPLE_DIMS)) * args.steps
-    value = total_links / sum(secs) / 1e9
-    sample = (f"one oracle step (force, momentum step, link step, action) of a "
+    reps = OracleReplicas()
+    try:
+        for _ in range(args.warmup):
+            reps.step(1)
+        rates, secs = [], []
+        for _ in range(args.steps):
+            r, s = reps.step(1)
+            rates.append(r)
+            secs.append(s)
+    finally:
+        reps.close()
+    value = statistics.mean(rates) / 1e9
+    sample = (f"per timed step, one oracle step (force, momentum step, link step, action) of a "
               f"{'x'.join(map(str, CPU_SAMPLE_DIMS))} lattice drawn like the {WORKLOAD} workload "
-              f"(w_a ~ N(0, 0.3^2), u0 0.87) per timed step; per-link work is volume independent")
+              f"(w_a ~ N(0, 0.3^2), u0 0.87) on each of {reps.workers} host cores, one "
+              f"independent single-threaded replica per core; per-link work is volume independent")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Glink/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * sum(secs) / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample_dims": list(CPU_SAMPLE_DIMS)},
-        "cpu_baseline": {"value": value, "unit": "Glink/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "Glink/s", "cores": reps.workers,
+                         "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "Glink/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }))
@@ -558,11 +598,20 @@ def run_ours(args):
     streaming["md_update_links"]["frac"] = streaming["md_update_links"]["gbs"] / hbm_peak
     cpu = None
     if world == 1 or rank == 0:
-        rate, secs = oracle_step_rate(steps=5)
-        cpu = {"value": rate / 1e9, "unit": "Glink/s", "cores": 1, "kind": "oracle",
-               "sample": f"5 oracle steps (force, momentum step, link step, action) of a "
+        rate1, secs1 = oracle_step_rate(steps=2)
+        reps = OracleReplicas()
+        try:
+            rate_all, secs_all = reps.step(3)
+        finally:
+            reps.close()
+        cpu = {"value": rate_all / 1e9, "unit": "Glink/s", "cores": reps.workers, "kind": "oracle",
+               "sample": f"3 oracle steps (force, momentum step, link step, action) of a "
                          f"{'x'.join(map(str, CPU_SAMPLE_DIMS))} lattice drawn like the "
-                         f"{WORKLOAD} workload, single-threaded, {secs:.1f} s"}
+                         f"{WORKLOAD} workload on each of {reps.workers} host cores (one "
+                         f"independent single-threaded replica per core, spawned processes), "
+                         f"{secs_all:.1f} s",
+               "single_core_value": rate1 / 1e9,
+               "single_core_sample": f"2 steps on one core, {secs1:.1f} s"}
     out = {
         "metric": METRIC, "value": value, "unit": "Glink/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -605,7 +654,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--force-variant", type=int, default=-1,
-                    help="fix the staple-field force schedule (0..4) instead of autotuning it "
+                    help="fix the staple-field force schedule (0..5) instead of autotuning it "
                          "at set-up; -1 (default) autotunes")
     args = ap.parse_args()
     if args.warmup < 3:
