@@ -275,6 +275,20 @@ LQCD_API int lqcd_convert_algebra(const lqcd_desc *desc, const void *src, int ds
 LQCD_API int lqcd_pack_links(const lqcd_desc *desc, const void *full, void *links, void *stream);
 LQCD_API int lqcd_unpack_links(const lqcd_desc *desc, const void *links, void *full, void *stream);
 
+/* lqcd_unitarity_deviation: max over links of the departure of the stored
+ * links from SU(3), evaluated in FP64 whatever desc->precision is:
+ * max(| |r0|^2 - 1 |, | |r1|^2 - 1 |, |<r0, r1>|, | |r2|^2 - 1 |) for the
+ * stored rows r0, r1 and the rebuilt r2 = conj(r0 x r1) (|r2|^2 = det U);
+ * zero exactly when U^dag U = 1 and det U = 1.  The check of FP32 links
+ * across a trajectory.  deviation: device double (8-byte aligned), written;
+ * workspace as for lqcd_kinetic_energy.  Deterministic.
+ * lqcd_reunitarise_links: Gram-Schmidt of rows 0 and 1 of every link (row 2
+ * is always rebuilt) computed in FP64 and rounded to desc->precision, in
+ * place.  Neither is in the paper (which fixes no reunitarisation). */
+LQCD_API int lqcd_unitarity_deviation(const lqcd_desc *desc, const void *links, double *deviation,
+                                      void *workspace, size_t workspace_bytes, void *stream);
+LQCD_API int lqcd_reunitarise_links(const lqcd_desc *desc, void *links, void *stream);
+
 /* Gaussian momenta for the momentum refresh of an HMC trajectory: every
  * component p^a_{n,mu} ~ N(0, 1), written in the algebra layout (device,
  * overwritten).  Counter-based, so the field depends only on `seed`:

@@ -113,6 +113,68 @@ __global__ void __launch_bounds__(kFinish) finish_sum(const double *partials, in
     }
 }
 
+// Departure of the stored links from SU(3), in FP64 whatever the storage
+// precision: with rows r0, r1 stored and r2 = conj(r0 x r1) rebuilt (so r2
+// is orthogonal to both and det U = |r2|^2), U^dag U = 1 and det U = 1 hold
+// exactly when |r0|^2 = |r1|^2 = 1 and <r0, r1> = 0; the measure is
+// max(| |r0|^2 - 1 |, | |r1|^2 - 1 |, |<r0, r1>|, | |r2|^2 - 1 |) over links.
+template <typename R> __global__ void __launch_bounds__(kBlock) unitarity_partials(const ReduceArgs a)
+{
+    const Geom g = make_geom(a.dims);
+    const R *__restrict__ links = static_cast<const R *>(a.links);
+    double worst = 0.0;
+    const int64_t nlinks = 4 * g.V;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nlinks;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int mu = (int)(i / g.V);
+        const int64_t n = i - mu * g.V;
+        const Mat<R> u = load_link(links, g.V, mu, n);
+        double n0 = 0.0, n1 = 0.0, cr = 0.0, ci = 0.0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const double ar = u.re[0][j], ai = u.im[0][j], br = u.re[1][j], bi = u.im[1][j];
+            n0 += ar * ar + ai * ai;
+            n1 += br * br + bi * bi;
+            cr += ar * br + ai * bi; // <r0, r1> = sum conj(a) b
+            ci += ar * bi - ai * br;
+        }
+        const double c2 = cr * cr + ci * ci;
+        const double d = fmax(fmax(fabs(n0 - 1.0), fabs(n1 - 1.0)),
+                              fmax(sqrt(c2), fabs(n0 * n1 - c2 - 1.0)));
+        worst = fmax(worst, d);
+    }
+    __shared__ double warp_part[kBlock / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_down_sync(0xffffffffu, worst, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) warp_part[warp] = worst;
+    __syncthreads();
+    if (warp == 0) {
+        double m = lane < kBlock / 32 ? warp_part[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+        if (lane == 0) a.partials[blockIdx.x] = m;
+    }
+}
+
+__global__ void __launch_bounds__(kFinish) finish_max(const double *partials, int count, double *out)
+{
+    __shared__ double warp_part[kFinish / 32];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < count; i += kFinish) v = fmax(v, partials[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) warp_part[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double m = warp_part[lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+        if (lane == 0) *out = m;
+    }
+}
+
 // Library-held scratch of the allocation-free action entry point: one double
 // per reduction block.  4096 doubles = 32 KiB, held by every device that
 // loads the library until the process exits.
@@ -165,6 +227,18 @@ cudaError_t launch_kinetic(const ReduceArgs &a, cudaStream_t st)
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     finish_sum<<<1, kFinish, 0, st>>>(a.partials, a.blocks, 1.0, a.out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unitarity(const ReduceArgs &a, cudaStream_t st)
+{
+    if (a.precision == LQCD_F64)
+        unitarity_partials<double><<<a.blocks, kBlock, 0, st>>>(a);
+    else
+        unitarity_partials<float><<<a.blocks, kBlock, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    finish_max<<<1, kFinish, 0, st>>>(a.partials, a.blocks, a.out);
     return cudaGetLastError();
 }
 

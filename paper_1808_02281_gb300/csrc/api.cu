@@ -450,6 +450,40 @@ int lqcd_kinetic_energy(const lqcd_desc *desc, const void *mom, double *energy, 
     return cuda_status(lqcd::launch_kinetic(a, as_stream(stream)));
 }
 
+int lqcd_unitarity_deviation(const lqcd_desc *desc, const void *links, double *deviation,
+                             void *workspace, size_t workspace_bytes, void *stream)
+{
+    LQCD_TRACE();
+    int s = check_desc(desc);
+    if (s) return s;
+    if ((s = check_ptrs({links}))) return s;
+    if (deviation == nullptr) return LQCD_ERR_ARG;
+    if (((uintptr_t)deviation & 7u) != 0) return LQCD_ERR_ALIGN;
+    int blocks = 0;
+    if ((s = reduction_setup(desc, workspace, workspace_bytes, &blocks))) return s;
+    lqcd::ReduceArgs a{};
+    copy_dims(a.dims, desc);
+    a.precision = desc->precision;
+    a.links = links;
+    a.partials = static_cast<double *>(workspace);
+    a.blocks = blocks;
+    a.out = deviation;
+    return cuda_status(lqcd::launch_unitarity(a, as_stream(stream)));
+}
+
+int lqcd_reunitarise_links(const lqcd_desc *desc, void *links, void *stream)
+{
+    LQCD_TRACE();
+    int s = check_desc(desc);
+    if (s) return s;
+    if ((s = check_ptrs({links}))) return s;
+    lqcd::MdArgs a{};
+    copy_dims(a.dims, desc);
+    a.precision = desc->precision;
+    a.links = links;
+    return cuda_status(lqcd::launch_reunitarise(a, as_stream(stream)));
+}
+
 int lqcd_md_update_momenta(const lqcd_desc *desc, void *mom, const void *force, double dt,
                            void *stream)
 {

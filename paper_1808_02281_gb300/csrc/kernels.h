@@ -123,6 +123,8 @@ cudaError_t launch_finish_sum(const double *partials, int count, double scale, d
                               cudaStream_t st);
 cudaError_t launch_action(const ReduceArgs &a, cudaStream_t st);
 cudaError_t launch_kinetic(const ReduceArgs &a, cudaStream_t st);
+// out = max over links of the FP64 departure of the stored links from SU(3).
+cudaError_t launch_unitarity(const ReduceArgs &a, cudaStream_t st);
 
 struct MdArgs {
     int dims[4];
@@ -153,6 +155,8 @@ cudaError_t launch_omega_gradient(const MdArgs &a, cudaStream_t st);
 cudaError_t launch_convert(const MdArgs &a, int dst_precision, bool links, cudaStream_t st);
 cudaError_t launch_pack(const MdArgs &a, cudaStream_t st);
 cudaError_t launch_unpack(const MdArgs &a, cudaStream_t st);
+// links <- Gram-Schmidt of rows 0 and 1 in FP64, rounded to the storage precision.
+cudaError_t launch_reunitarise(const MdArgs &a, cudaStream_t st);
 // mom_out <- Gaussian momenta of stream a.seed (SplitMix64 + Box-Muller).
 cudaError_t launch_gaussian_momenta(const MdArgs &a, cudaStream_t st);
 

@@ -281,6 +281,37 @@ __global__ void __launch_bounds__(kBlock) unpack(const R *__restrict__ links, R 
     }
 }
 
+// Gram-Schmidt of rows 0 and 1 of every stored link in FP64 (row 2 is
+// rebuilt on every load), rounded back to the storage precision.
+template <typename R> __global__ void __launch_bounds__(kBlock) reunitarise_fp64(R *__restrict__ links, int64_t V)
+{
+    const int64_t nlinks = 4 * V;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nlinks;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int mu = (int)(i / V);
+        const int64_t n = i - mu * V;
+        const Mat<R> u = load_link(links, V, mu, n);
+        Mat<double> w;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                w.re[r][j] = (double)u.re[r][j];
+                w.im[r][j] = (double)u.im[r][j];
+            }
+        reunitarise(w);
+        Mat<R> v;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                v.re[r][j] = (R)w.re[r][j];
+                v.im[r][j] = (R)w.im[r][j];
+            }
+        store_link(links, V, mu, n, v);
+    }
+}
+
 // Word i of the counter-based SplitMix64 stream `seed` (Steele, Lea & Flood,
 // "Fast splittable pseudorandom number generators", OOPSLA 2014):
 // mix(seed + (i + 1) * golden gamma) with the published finaliser.
@@ -320,6 +351,16 @@ __global__ void __launch_bounds__(kBlock) gaussian_momenta(R *__restrict__ mom, 
 }
 
 } // namespace
+
+cudaError_t launch_reunitarise(const MdArgs &a, cudaStream_t st)
+{
+    const int64_t V = volume(a.dims);
+    if (a.precision == LQCD_F64)
+        reunitarise_fp64<double><<<grid_for(4 * V), kBlock, 0, st>>>(static_cast<double *>(a.links), V);
+    else
+        reunitarise_fp64<float><<<grid_for(4 * V), kBlock, 0, st>>>(static_cast<float *>(a.links), V);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_gaussian_momenta(const MdArgs &a, cudaStream_t st)
 {

@@ -17,8 +17,9 @@ stored values.  A whole trajectory can be captured as one CUDA graph.
 A full HMC run (``run_hmc``) adds to each trajectory the momentum refresh
 (Gaussian momenta drawn on the GPU from a counter-based stream), the
 Metropolis test accept with probability min(1, exp(-dH)) (the links are
-restored on rejection) and a record per trajectory (dH, acceptance, action,
-plaquette); ``save_checkpoint`` / ``load_checkpoint`` store and restore the
+restored on rejection), an optional FP64 reunitarisation of the links every
+N trajectories, and a record per trajectory (dH, acceptance, action,
+plaquette, the FP64 unitarity deviation of the links); ``save_checkpoint`` / ``load_checkpoint`` store and restore the
 state so that a resumed run continues bit for bit.
 
 ``python -m paper_1808_02281_gb300.hmc`` runs the dH-versus-dt study;
@@ -263,6 +264,7 @@ class HMCConfig:
     integrator: str = "omelyan"
     seed: int = 1
     action_precision: str | None = None   # "f64" for FP32 runs: Metropolis on the FP64 action
+    reunitarise_every: int = 0            # > 0: FP64 Gram-Schmidt of the links every N trajectories
 
 
 def _stream_word(seed: int, i: int) -> int:
@@ -293,9 +295,12 @@ def hmc_trajectory(st: MDState, cfg: HMCConfig, trajectory: int) -> dict:
     if not accept:
         st.links.copy_(saved)
     del saved
+    if cfg.reunitarise_every and (trajectory + 1) % cfg.reunitarise_every == 0:
+        lqcd.reunitarise_links(st.lat, st.links)
     S = float(lqcd.gauge_action(st.lat, st.links, workspace=st.workspace).item())
+    unitarity = float(lqcd.unitarity_deviation(st.lat, st.links, workspace=st.workspace).item())
     return {"trajectory": trajectory, "dH": dH, "accepted": bool(accept), "action": S,
-            "plaquette": plaquette(st), "nsteps": nsteps,
+            "plaquette": plaquette(st), "unitarity": unitarity, "nsteps": nsteps,
             "forces": force_evaluations(cfg.integrator, nsteps),
             "seconds": time.perf_counter() - t0}
 

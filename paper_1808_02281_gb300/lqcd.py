@@ -87,6 +87,9 @@ _EXPORTS = {
     "lqcd_wilson_hopping_force": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
                                                  ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]),
+    "lqcd_unitarity_deviation": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "lqcd_reunitarise_links": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p]),
     "lqcd_gaussian_momenta": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_uint64, ctypes.c_void_p,
                                              ctypes.c_void_p]),
     "lqcd_measure_fma_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
@@ -269,6 +272,27 @@ def wilson_hopping_force(lat: Lattice, links: torch.Tensor, X: torch.Tensor, Y: 
     return force
 
 
+def unitarity_deviation(lat: Lattice, links: torch.Tensor, out: torch.Tensor | None = None,
+                        workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """max over links of the FP64 departure of the stored links from SU(3)
+    (0-d float64 device tensor)."""
+    _check(links, lat, lat.link_shape, "links")
+    out = torch.empty((), dtype=torch.float64, device=links.device) if out is None else out
+    ws = reduction_workspace(links.device) if workspace is None else workspace
+    d = lat.desc()
+    _call("lqcd_unitarity_deviation", ctypes.byref(d), _ptr(links), _ptr(out), _ptr(ws),
+          ws.numel(), _stream(stream))
+    return out
+
+
+def reunitarise_links(lat: Lattice, links: torch.Tensor, stream=None) -> torch.Tensor:
+    """Gram-Schmidt of every link in FP64, rounded to the storage precision (in place)."""
+    _check(links, lat, lat.link_shape, "links")
+    d = lat.desc()
+    _call("lqcd_reunitarise_links", ctypes.byref(d), _ptr(links), _stream(stream))
+    return links
+
+
 def gaussian_momenta(lat: Lattice, seed: int, out: torch.Tensor | None = None,
                      device=None, stream=None) -> torch.Tensor:
     """p^a ~ N(0, 1) on every link from the counter-based stream `seed`
@@ -295,6 +319,15 @@ def measure_fma_rate(precision: str = "f32", device=None, stream=None) -> float:
 def workspace_bytes(lat: Lattice) -> int:
     d = lat.desc()
     return int(_lib().lqcd_workspace_bytes(ctypes.byref(d)))
+
+
+REDUCTION_WORKSPACE_BYTES = 1 << 16   # partial sums of up to 8192 reduction blocks
+
+
+def reduction_workspace(device=None) -> torch.Tensor:
+    """Workspace enough for the reductions alone (action, kinetic energy,
+    unitarity check): one double per reduction block."""
+    return torch.empty(REDUCTION_WORKSPACE_BYTES, dtype=torch.uint8, device=device or "cuda")
 
 
 def make_workspace(lat: Lattice, device=None) -> torch.Tensor:
@@ -372,7 +405,7 @@ def gauge_action(lat: Lattice, links: torch.Tensor, out: torch.Tensor | None = N
     """S_G (FP64, 0-d device tensor), Eq. 18_6_4_1."""
     _check(links, lat, lat.link_shape, "links")
     out = torch.empty((), dtype=torch.float64, device=links.device) if out is None else out
-    ws = make_workspace(lat, links.device) if workspace is None else workspace
+    ws = reduction_workspace(links.device) if workspace is None else workspace
     d = lat.desc()
     _call("lqcd_gauge_action", ctypes.byref(d), _ptr(links), _ptr(out), _ptr(ws), ws.numel(),
           _stream(stream))
@@ -384,7 +417,7 @@ def kinetic_energy(lat: Lattice, mom: torch.Tensor, out: torch.Tensor | None = N
     """K = sum p^2 / 2 (FP64, 0-d device tensor)."""
     _check(mom, lat, lat.algebra_shape, "mom")
     out = torch.empty((), dtype=torch.float64, device=mom.device) if out is None else out
-    ws = make_workspace(lat, mom.device) if workspace is None else workspace
+    ws = reduction_workspace(mom.device) if workspace is None else workspace
     d = lat.desc()
     _call("lqcd_kinetic_energy", ctypes.byref(d), _ptr(mom), _ptr(out), _ptr(ws), ws.numel(),
           _stream(stream))

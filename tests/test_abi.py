@@ -130,6 +130,18 @@ def test_wilson_argument_checks(lib):
                  None) == -1
 
 
+def test_unitarity_and_reunitarise_argument_checks(lib):
+    d = _desc()
+    assert lib.lqcd_unitarity_deviation(ctypes.byref(d), None, GOOD2, GOOD, 4096, None) == -1
+    assert lib.lqcd_unitarity_deviation(ctypes.byref(d), GOOD, None, GOOD, 4096, None) == -1
+    assert lib.lqcd_unitarity_deviation(ctypes.byref(d), MISALIGNED, GOOD2, GOOD, 4096, None) == -3
+    assert lib.lqcd_unitarity_deviation(ctypes.byref(_desc(dims=(0, 4, 4, 4))), GOOD, GOOD2, GOOD,
+                                        4096, None) == -2
+    assert lib.lqcd_reunitarise_links(ctypes.byref(d), None, None) == -1
+    assert lib.lqcd_reunitarise_links(ctypes.byref(d), MISALIGNED, None) == -3
+    assert lib.lqcd_reunitarise_links(None, GOOD, None) == -1
+
+
 def test_fma_rate_argument_checks(lib):
     out = ctypes.c_double()
     n = lib.lqcd_fma_rate_scratch_bytes()

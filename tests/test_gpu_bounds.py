@@ -95,6 +95,14 @@ def test_gauge_entry_points_stay_in_bounds(dims, prec):
     u = Padded(lat.link_shape, lat.dtype, fill=links)
     lqcd.md_update_links(lat, u.view, mom0, 0.02)
     assert u.margins_intact()
+    lqcd.reunitarise_links(lat, u.view)
+    assert u.margins_intact()
+    dev = Padded((), torch.float64)
+    lqcd.unitarity_deviation(lat, links, out=dev.view, workspace=ws.view)
+    assert dev.margins_intact() and ws.margins_intact()
+    m2 = Padded(lat.algebra_shape, lat.dtype)
+    lqcd.gaussian_momenta(lat, 5, out=m2.view)
+    assert m2.margins_intact()
     g = Padded(lat.algebra_shape, lat.dtype)
     lqcd.omega_gradient(lat, omega, f0, out=g.view)
     assert g.margins_intact()

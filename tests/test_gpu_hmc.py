@@ -166,3 +166,46 @@ def test_resume_from_checkpoint_is_bitwise(tmp_path):
     for a, b in zip(full, first + rest):
         assert a["dH"] == b["dH"] and a["accepted"] == b["accepted"] and a["action"] == b["action"]
     assert sum(r["accepted"] for r in full) >= 3    # small dt: nearly every trajectory accepted
+
+
+def _perturbed(lat, U, scale0=1.0, mix=0.0):
+    """The stored rows changed on the host: row 0 scaled, row 1 += mix * row 0."""
+    full = lqcd.unpack_links(lat, U).clone()
+    full[..., 0, :, :] *= scale0
+    full[..., 1, :, :] += mix * full[..., 0, :, :]
+    return lqcd.pack_links(lat, full)
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-14), ("f32", 1e-6)])
+def test_unitarity_deviation_closed_forms(prec, tol):
+    st = _state(prec)
+    lat = st.lat
+    assert float(lqcd.unitarity_deviation(lat, st.links).item()) < tol
+    s = 1.0 + 3e-3
+    got = float(lqcd.unitarity_deviation(lat, _perturbed(lat, st.links, scale0=s)).item())
+    assert abs(got - (s * s - 1.0)) < 10 * tol
+    d = 2e-3
+    got = float(lqcd.unitarity_deviation(lat, _perturbed(lat, st.links, mix=d)).item())
+    assert abs(got - d) < 10 * tol
+
+
+def test_reunitarise_matches_oracle_gram_schmidt():
+    """FP64: the GPU's FP64 Gram-Schmidt of perturbed links equals the
+    oracle's (its link step with zero momenta is exp(0) U, reunitarised)."""
+    st = _state("f64")
+    lat = st.lat
+    P = _perturbed(lat, st.links, scale0=1.01, mix=0.02)
+    full = lqcd.full_from_device(lqcd.unpack_links(lat, P))
+    want = O.md_update_links(full, np.zeros((256, 4, 8)), 0.0)
+    lqcd.reunitarise_links(lat, P)
+    got = lqcd.full_from_device(lqcd.unpack_links(lat, P))
+    assert np.abs(got - want).max() < 1e-14
+    assert float(lqcd.unitarity_deviation(lat, P).item()) < 1e-14
+
+
+def test_reunitarise_fp32_links_in_fp64():
+    st = _state("f32")
+    P = _perturbed(st.lat, st.links, scale0=1.01, mix=0.02)
+    assert float(lqcd.unitarity_deviation(st.lat, P).item()) > 1e-2
+    lqcd.reunitarise_links(st.lat, P)
+    assert float(lqcd.unitarity_deviation(st.lat, P).item()) < 1e-6
