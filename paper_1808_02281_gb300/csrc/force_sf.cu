@@ -266,14 +266,17 @@ __device__ __forceinline__ void staples_block(const SfLattice &L, const Geom &g,
         const int nu = (mu + 1 + iv) & 3;
         const int64_t vp = disp(g, c, nu, 1), vm = disp(g, c, nu, -1);
         // b = +nu:  U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
+        // rows 0 and 1 of each staple (which need rows 0 and 1 of the first
+        // product only); a full plane takes its third row from them, the
+        // staple being a product of three SU(3) links
         Mat<R> t = mul<N, D>(load_link(links, g.V, nu, xm), load_link(links, g.V, mu, x + vp));
-        const Mat<R> up = FULL ? mul<N, D>(t, load_link(links, g.V, nu, x))
-                               : mul_top2<N, D>(t, load_link(links, g.V, nu, x));
+        Mat<R> up = mul_top2<N, D>(t, load_link(links, g.V, nu, x));
+        if constexpr (FULL) rebuild_row2(up);
         Staples<R, FULL>::store(sf, g.V, mu * 6 + 2 * iv, x, up);
         // b = -nu:  U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu)
         t = mul<D, D>(load_link(links, g.V, nu, xm + vm), load_link(links, g.V, mu, x + vm));
-        const Mat<R> dn = FULL ? mul<N, N>(t, load_link(links, g.V, nu, x + vm))
-                               : mul_top2<N, N>(t, load_link(links, g.V, nu, x + vm));
+        Mat<R> dn = mul_top2<N, N>(t, load_link(links, g.V, nu, x + vm));
+        if constexpr (FULL) rebuild_row2(dn);
         Staples<R, FULL>::store(sf, g.V, mu * 6 + 2 * iv + 1, x, dn);
     }
 }
