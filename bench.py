@@ -71,10 +71,15 @@ def _peaks():
 
 
 def _source_digest() -> str:
+    """Digest of the force kernels' code (comments and whitespace stripped,
+    so that only a change of the code itself invalidates a recorded profile)."""
     h = hashlib.sha256()
     for f in ("force_sf.cu", "su3.cuh"):
-        with open(os.path.join(ROOT, "paper_1808_02281_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1808_02281_gb300", "csrc", f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

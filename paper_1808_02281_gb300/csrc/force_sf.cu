@@ -4,9 +4,11 @@
 // Pass A (staple_fields) stores, for every link (x, mu) and every signed
 // direction b perpendicular to mu, the plaquette staple
 //     S^{(mu)}_b(x) = link(x+mu, b) U_mu(x+b)^dag link(x, b)^dag
-// (the path x+mu -> x+mu+b -> x+b -> x).  It is a product of three SU(3)
-// matrices, so it is SU(3) and is stored in the compact two-row form, like a
-// link: 24 "directions" per site instead of 4.
+// (the path x+mu -> x+mu+b -> x+b -> x): 24 "directions" per site instead
+// of 4.  It is a product of three SU(3) matrices, so it is SU(3): its first
+// two rows (which need only two rows of the first product) determine the
+// third, conj(row0 x row1).  Planes are stored compact (two rows, the third
+// rebuilt on load, like links) or full (all 18 reals; the default schedule).
 //
 // Pass B (force_from_staples) builds every staple of the link (k, rho) from
 // those fields.  With S = S^{(rho)} and A_b = link(k, b), B_b = link(k+rho, b),
@@ -22,7 +24,9 @@
 //   t = c_plaq sum_b S_b(k) + c_rect (F sum_b S_b(k+rho) S_b(k) + sum_b S_b(k) S_b(k-rho) E)
 //     + sum_d B_d [ c_cube sum_{b perp d} S_b(k+d) S^{(d)}_b(k) + c_rect S_d(k+d) A_d^dag ],
 // 51 SU(3) products per link in pass B and 12 (10 stored rows) per link in
-// pass A, against 180 for the 48 staples walked one by one.
+// pass A, against 180 for the 48 staples walked one by one.  Every product
+// of two SU(3) factors in pass B likewise forms two rows and takes its third
+// from them, so the left factor's third row is never needed.
 //
 // The action comes out of pass B at no extra products: summing
 // Re tr(U_{k,rho} t_{k,rho}) over links counts every loop once per link on it
