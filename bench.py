@@ -659,7 +659,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--force-variant", type=int, default=-1,
-                    help="fix the staple-field force schedule (0..5) instead of autotuning it "
+                    help="fix the staple-field force schedule (0..6) instead of autotuning it "
                          "at set-up; -1 (default) autotunes")
     args = ap.parse_args()
     if args.warmup < 3:

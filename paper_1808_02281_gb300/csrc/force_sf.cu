@@ -511,15 +511,19 @@ unsigned grid_of(int64_t items)
 //   1  micro-tiles 8x2x2, inner b loop unrolled
 //   2  x rows (no micro-tiles), inner b loop rolled
 //   3  x rows, registers capped for 4 CTAs/SM also with the fused action
-//   4  x rows, staple planes stored full (18 reals, no row rebuilt on load)
-//   5  x rows, full staple planes, registers capped for 4 CTAs/SM
+//   4  x rows, staple planes stored full (18 reals, no row rebuilt on load),
+//      spatial blocks up to 64x8x8 (full planes are 1.5x the bytes per site:
+//      smaller blocks keep the sweep's working set in L2; 4.22 against
+//      4.45 ms with 64x16x16 at 32^3x64 FP32)
+//   5  as 4, registers capped for 4 CTAs/SM
+//   6  as 4 with spatial blocks up to 64x16x16
 // The process-wide choice per precision is set by lqcd_set_force_variant or
 // lqcd_autotune_force; -1 means the default: x rows with full staples in both
 // precisions (at 32^3x64: FP32 4.64 vs 4.75 ms with compact staples, FP64
 // 114 vs 128 ms).
-constexpr int kSfVariants = 6;
+constexpr int kSfVariants = 7;
 
-bool full_staples(int variant) { return variant == 4 || variant == 5; }
+bool full_staples(int variant) { return variant >= 4; }
 
 // Slot of a kernel instance in the occupancy cache of persistent_grid:
 // kind (0 pass B, 1 pass B capped, 2 pass B full, 3 pass B full capped,
@@ -541,9 +545,10 @@ int block_extent(int L, int cap)
 
 void set_traversal(SfLattice &L, int variant)
 {
+    const int cap_yz = (variant == 4 || variant == 5) ? 8 : 16;
     L.sweep[0] = block_extent(L.dims[0], 64);
-    L.sweep[1] = block_extent(L.dims[1], 16);
-    L.sweep[2] = block_extent(L.dims[2], 16);
+    L.sweep[1] = block_extent(L.dims[1], cap_yz);
+    L.sweep[2] = block_extent(L.dims[2], cap_yz);
     if (variant >= 2) {
         L.micro[0] = L.sweep[0];
         L.micro[1] = L.micro[2] = 1;
@@ -603,7 +608,7 @@ cudaError_t launch_pass_b(const SfLattice &L, const KernelScalars &sc, int varia
     const unsigned grid = grid_of(virtual_blocks((int64_t)L.dims[0] * L.dims[1] * L.dims[2] * L.dims[3]));
     if (variant == 1) force_from_staples<R, ACTION, true><<<grid, kBlock, 0, st>>>(L, sc);
     else if (variant == 3) force_from_staples<R, ACTION, false, true><<<grid, kBlock, 0, st>>>(L, sc);
-    else if (variant == 4)
+    else if (variant == 4 || variant == 6)
         force_from_staples<R, ACTION, false, false, true><<<grid, kBlock, 0, st>>>(L, sc);
     else if (variant == 5)
         force_from_staples<R, ACTION, false, true, true><<<grid, kBlock, 0, st>>>(L, sc);
@@ -622,7 +627,7 @@ cudaError_t launch_pass_b_batched(const SfBatch &B, const KernelScalars &sc, int
     } else if (variant == 3) {
         auto k = force_from_staples_batched<R, ACTION, false, true>;
         k<<<persistent_grid(k, grid_slot(1, f64, ACTION, false), B.total), kBlock, 0, st>>>(B, sc);
-    } else if (variant == 4) {
+    } else if (variant == 4 || variant == 6) {
         auto k = force_from_staples_batched<R, ACTION, false, false, true>;
         k<<<persistent_grid(k, grid_slot(2, f64, ACTION, false), B.total), kBlock, 0, st>>>(B, sc);
     } else if (variant == 5) {
