@@ -321,6 +321,60 @@ def run_hmc(st: MDState, cfg: HMCConfig, n: int, start: int = 0, checkpoint: str
         yield rec
 
 
+def batch_hamiltonians(bs: BatchState, action_precision: str | None = None) -> list:
+    """H = K + S (FP64) of every lattice of the batch."""
+    out = []
+    for c, d in enumerate(bs.dims):
+        lat = bs.params.with_(dims=d)
+        st = MDState(lat, bs.links[c], bs.mom[c], bs.workspace)
+        out.append(hamiltonian(st, action_precision))
+    return out
+
+
+def lattice_config(cfg: HMCConfig, c: int) -> HMCConfig:
+    """Settings of lattice c of a batch run: its own generator streams
+    (seed + 2c), so that lattice c of a batch run equals a single-lattice run
+    with these settings."""
+    return dataclasses.replace(cfg, seed=cfg.seed + 2 * c)
+
+
+def batch_hmc_trajectory(bs: BatchState, cfg: HMCConfig, trajectory: int) -> list:
+    """One HMC trajectory of every lattice of the batch: per-lattice
+    momentum refresh, one batched integration (one launch per pass for all
+    lattices), per-lattice Metropolis test and restore.  One record per
+    lattice."""
+    t0 = time.perf_counter()
+    cfgs = [lattice_config(cfg, c) for c in range(len(bs.dims))]
+    for c, d in enumerate(bs.dims):
+        lqcd.gaussian_momenta(bs.params.with_(dims=d), momentum_seed(cfgs[c], trajectory),
+                              out=bs.mom[c])
+    saved = [u.clone() for u in bs.links]
+    nsteps = max(1, int(round(cfg.tau / cfg.dt)))
+    H0 = batch_hamiltonians(bs, cfg.action_precision)
+    BATCH_INTEGRATORS[cfg.integrator](bs, cfg.tau / nsteps, nsteps)
+    H1 = batch_hamiltonians(bs, cfg.action_precision)
+    recs = []
+    for c, d in enumerate(bs.dims):
+        dH = H1[c] - H0[c]
+        accept = metropolis_uniform(cfgs[c], trajectory) < math.exp(min(0.0, -dH))
+        if not accept:
+            bs.links[c].copy_(saved[c])
+        recs.append({"trajectory": trajectory, "lattice": c, "dims": list(d), "dH": dH,
+                     "accepted": bool(accept), "nsteps": nsteps})
+    del saved
+    secs = time.perf_counter() - t0
+    for r in recs:
+        r["seconds"] = secs
+    return recs
+
+
+def run_hmc_batch(bs: BatchState, cfg: HMCConfig, n: int, start: int = 0):
+    """Trajectories start .. start+n-1 of every lattice; yields the list of
+    per-lattice records of each trajectory."""
+    for i in range(n):
+        yield batch_hmc_trajectory(bs, cfg, start + i)
+
+
 # ----------------------------------------------------------- checkpoints
 
 _MAGIC = b"LQCDCKPT"

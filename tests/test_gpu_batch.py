@@ -116,3 +116,22 @@ def test_batch_trajectory_graph_equals_eager_and_single():
         assert torch.equal(bs.mom[c], eager.mom[c])
         assert torch.equal(eager.links[c], singles[c].links)
         assert torch.equal(eager.mom[c], singles[c].mom)
+
+
+def test_batch_hmc_equals_single_runs():
+    """Lattice c of a batch HMC run equals a single-lattice run with the
+    settings lattice_config(cfg, c): same dH, same decisions, same links."""
+    dims_list = MIXED[:3]
+    cfg = hmc.HMCConfig(tau=0.2, dt=0.05, integrator="leapfrog", seed=11)
+    bs = hmc.initial_batch(dims_list, "f64", sigma=0.4, seed=3)
+    singles = []
+    for c, d in enumerate(bs.dims):
+        lat = bs.params.with_(dims=d)
+        singles.append(hmc.MDState.create(lat, bs.links[c].clone(), bs.mom[c].clone()))
+    recs = [r for step in hmc.run_hmc_batch(bs, cfg, 2) for r in step]
+    for c, st in enumerate(singles):
+        mine = list(hmc.run_hmc(st, hmc.lattice_config(cfg, c), 2))
+        theirs = [r for r in recs if r["lattice"] == c]
+        for a, b in zip(mine, theirs):
+            assert a["dH"] == b["dH"] and a["accepted"] == b["accepted"], (c, a, b)
+        assert torch.equal(st.links, bs.links[c]), c
