@@ -1,12 +1,14 @@
 /*
  * liblqcd -- GB300 (sm_103a) molecular-dynamics hot path of the one-loop
  * Symanzik improved gauge action (D. Li, "The Calculation of Force in Lattice
- * Quantum Chromodynamics", Sec. II).
+ * Quantum Chromodynamics", Sec. II), and the hopping operator of the Wilson
+ * fermion matrix with its force on the links (Sec. III).
  *
  * C ABI: plain pointers and sizes.  Device buffers are owned by the caller;
  * no entry point allocates device memory, and none synchronises the device
- * (every kernel is enqueued on the caller's stream, `stream` = a
- * cudaStream_t, NULL for the legacy default stream).  Every entry point
+ * except the two that time kernels (lqcd_autotune_force,
+ * lqcd_measure_fma_rate); every kernel is enqueued on the caller's stream
+ * (`stream` = a cudaStream_t, NULL for the legacy default stream).  Every entry point
  * returns LQCD_OK (0) or a negative LQCD_ERR_* code; arguments are checked
  * before anything is enqueued, so on an argument error no output is touched.
  * LQCD_ERR_CUDA reports a failed launch (the CUDA error is kept for
