@@ -2,17 +2,18 @@
  * Plain FP64 CPU oracle for the one-loop Symanzik improved gauge action, its
  * molecular-dynamics force and the MD momentum / link updates that use it
  * (D. Li, "The Calculation of Force in Lattice Quantum Chromodynamics",
- * Sec. II, Eqs. 18_3_27_30 ... 18_6_6_13 and the force algorithm that follows
- * Eq. 18_6_6_13), and the hopping operator of the Wilson fermion matrix with
- * its force on the links (Sec. III, Eqs. 18_7_17_4 and 18_1_29_19 ...
- * 18_7_17_30).
+ * Sec. II, Eqs. 18_3_27_30 ... 18_6_6_13), and the hopping operator of the
+ * Wilson fermion matrix with its force on the links (Sec. III, Eqs. 18_7_17_4
+ * and 18_1_29_19 ... 18_7_17_30).
  *
  * TEST INFRASTRUCTURE ONLY.  This file is the independent checker of the CUDA
  * library: only the test-suite, the smoke check and the CPU-baseline leg of
  * the benchmark may load it.  It shares no code, header, table or constant
- * with the CUDA sources.  It is deliberately slow: every step is written out
- * in the order and notation of the paper, with C99 complex arithmetic, no
- * blocking, no fusion and no reordering beyond what the equations state.
+ * with the CUDA sources.  It is deliberately slow: every quantity is the
+ * paper's definition written out in its notation -- the action as the sum of
+ * the 34 loop traces at every site, the force on each link as the derivative
+ * of the loops through that link -- with C99 complex arithmetic, no blocking,
+ * no fusion and no reordering beyond what the equations state.
  *
  * Conventions.
  *   - Directions are numbered 1..4 as in the paper (x, y, z, t).  A signed
@@ -31,8 +32,9 @@
  * finite differences along all 8 generators, the Wilson-action limit against
  * an independent staple formula, uniform-link configurations against a
  * brute-force single-site sum, the identity of Eq. 18_6_6_13, the exponential
- * against scipy.linalg.expm, and leapfrog energy conservation/reversibility;
- * for Sec. III: the Clifford algebra of the gamma basis, the free-field
+ * against scipy.linalg.expm, the reunitarisation against Gram-Schmidt (a QR
+ * factorisation) on links that are not unitary, and leapfrog energy
+ * conservation/reversibility; for Sec. III: the Clifford algebra of the gamma basis, the free-field
  * (unit-link) plane-wave spectrum of the hopping operator, its gamma_5
  * hermiticity, gauge covariance, and finite differences of
  * 2 Re Y^dag calD X along all 8 generators against the hopping force.
@@ -400,11 +402,20 @@ double oracle_gauge_action_local(const int dims[4], const double *U, double beta
 
 /* -------------------------------------------------------- force (a4, a5) */
 
-/* Staple of occurrence l (0-based) of path p started at n, with the sites
- * pos[] it visits:
- *   d_l = +rho:  U_{n_{l+1},d_{l+1}} ... U_{n_L,d_L} U_{n_1,d_1} ... U_{n_{l-1},d_{l-1}}
- *   d_l = -rho:  U^dag_{n_{l-1},d_{l-1}} ... U^dag_{n_1,d_1} U^dag_{n_L,d_L} ... U^dag_{n_{l+1},d_{l+1}}
- * (the two bracketed products of Eq. 18_7_25_2). */
+/* What one loop through the link (k, rho) contributes to its derivative.
+ * The loop P_n holds the link at position l (0-based), either as U_{k,rho}
+ * itself (d_l = +rho, n_l = k) or as its inverse U_{k,rho}^dag = U_{k+rho,-rho}
+ * (d_l = -rho, n_l = k + rho).  Write P_n = A U B or A U^dag B, with A the
+ * factors before position l and B those after it.  Under the left
+ * perturbation U -> exp(i eps T_a) U (Eqs. 18_7_26_1 to 18_7_26_3) the factor
+ * becomes i T_a U, or U^dag (-i T_a), and the cyclic property of the trace
+ * brings the link to the front:
+ *   d/deps Re tr(A U B)     = Re tr(i T_a U (B A)),
+ *   d/deps Re tr(A U^dag B) = Re tr(-i T_a B A U^dag) = Re tr(i T_a U (B A)^dag),
+ * the last by Re tr M = Re tr M^dag.  Every loop through the link therefore
+ * gives Re tr(i T_a U W); W = B A (forward) or (B A)^dag = A^dag B^dag
+ * (backward) are the two staples of Eq. 18_7_25_2, returned here from the
+ * sites pos[] that the loop visits. */
 static mat3 staple(const field *f, const path *p, const long pos[6], int l, int forward)
 {
     mat3 m = unit3();
@@ -419,74 +430,63 @@ static mat3 staple(const field *f, const path *p, const long pos[6], int l, int 
     return m;
 }
 
-/* f^a = 2 tr(T_a H) with H = (beta/6) i (U_{k,rho} t_{k,rho})_TA, the last
- * step of the force algorithm (Eqs. 18_7_25_2, 18_6_6_11, 18_6_6_13). */
+/* f^a = 2 tr(T_a H) with H = (beta/6) i (U_{k,rho} t_{k,rho})_TA
+ * (Eqs. 18_7_25_2, 18_6_6_11, 18_6_6_13). */
 static void project(mat3 u, mat3 t, double beta, double out[8])
 {
     mat3 h = scale(I * beta / 6.0, traceless_antihermitian(mul(u, t)));
     for (int a = 0; a < 8; ++a) out[a] = 2.0 * creal(trace(mul(generator(a), h)));
 }
 
-/* The force algorithm after Eq. 18_6_6_13, step by step:
- *   for every direction rho: t_{k,rho} = 0 for all k;
- *     for each of the 34 paths P, for each link l of P:
- *       d_l = +rho: t_{k,rho} += c_P (forward staple) for all sites k = n_l;
- *       d_l = -rho: t_{k,rho} += c_P (backward staple) for all sites k = n_l - rho;
- *     then (beta/6) i (U_{k,rho} t_{k,rho})_TA for every k.
- * Output f[V][4][8] (see project()). */
+/* The force on the link (k, rho) from its definition, Eq. 18_7_25_1,
+ *   H_{k,rho} = -sum_a T_a dS/domega^a_{k,rho},
+ *   S = (beta/3) sum_P sum_n c_P [3 - Re tr P_n]                 (Eq. 18_6_4_1).
+ * Only the loops through the link depend on omega_{k,rho}.  For a loop
+ * shape P and a position l with d_l = +-rho exactly one start site puts the
+ * link at position l:
+ *   n = k - sum_{j<l} hat(d_j)             (d_l = +rho, Eq. 18_7_26_2),
+ *   n = k + hat(rho) - sum_{j<l} hat(d_j)  (d_l = -rho, Eq. 18_7_26_3).
+ * With the staples W of these loops (staple() above),
+ *   -dS/domega^a = (beta/3) sum c_P Re tr(i T_a U W) = (beta/3) Re tr(i T_a U t),
+ * t = sum c_P W, and the identity of Eq. 18_6_6_13,
+ * sum_a T_a Re tr(i T_a B) = (1/2) i B_TA, gives H = (beta/6) i (U t)_TA. */
+static void link_force(const field *f, const path p[34], int np, double beta, const double c[3],
+                       long k, int rho, double out[8])
+{
+    mat3 t = zero3();
+    for (int ip = 0; ip < np; ++ip)
+        for (int l = 0; l < p[ip].len; ++l) {
+            int dl = p[ip].d[l];
+            if (dl != rho && dl != -rho) continue;
+            long n = (dl == rho) ? k : step(&f->g, k, rho);
+            for (int j = 0; j < l; ++j) n = step(&f->g, n, -p[ip].d[j]);
+            long pos[6];
+            visit(&f->g, &p[ip], n, pos);
+            t = add(t, scale(c[p[ip].cls], staple(f, &p[ip], pos, l, dl == rho)));
+        }
+    project(get_link(f, k, rho), t, beta, out);
+}
+
+/* The force on every link, link by link.  Output f[V][4][8] (see project()). */
 void oracle_gauge_force(const int dims[4], const double *U, double beta, const double c[3],
                         double *fout)
 {
     field f = {make_geom(dims), (const cplx *)U};
     path p[34];
     int np = build_paths(p);
-    mat3 *t = (mat3 *)malloc(sizeof(mat3) * (size_t)f.g.V);
-    for (int rho = 1; rho <= 4; ++rho) {
-        for (long k = 0; k < f.g.V; ++k) t[k] = zero3();
-        for (int ip = 0; ip < np; ++ip)
-            for (int l = 0; l < p[ip].len; ++l) {
-                int dl = p[ip].d[l];
-                if (dl != rho && dl != -rho) continue;
-                for (long n = 0; n < f.g.V; ++n) {
-                    long pos[6];
-                    visit(&f.g, &p[ip], n, pos);
-                    if (dl == rho) {
-                        long k = pos[l];
-                        t[k] = add(t[k], scale(c[p[ip].cls], staple(&f, &p[ip], pos, l, 1)));
-                    } else {
-                        long k = step(&f.g, pos[l], -rho);
-                        t[k] = add(t[k], scale(c[p[ip].cls], staple(&f, &p[ip], pos, l, 0)));
-                    }
-                }
-            }
-        for (long k = 0; k < f.g.V; ++k)
-            project(get_link(&f, k, rho), t[k], beta, fout + ((size_t)k * 4 + (rho - 1)) * 8);
-    }
-    free(t);
+    for (long k = 0; k < f.g.V; ++k)
+        for (int rho = 1; rho <= 4; ++rho)
+            link_force(&f, p, np, beta, c, k, rho, fout + ((size_t)k * 4 + (rho - 1)) * 8);
 }
 
-/* Force on the single link (k, rho): the same staples, found from the link
- * instead of from the path start.  The start site of the path is
- *   n = k - sum_{j<l} hat(d_j)          if d_l = +rho   (Eq. 18_7_26_2)
- *   n = k + hat(rho) - sum_{j<l} hat(d_j)  if d_l = -rho (Eq. 18_7_26_3). */
+/* The force on the single link (k, rho = 1..4). */
 void oracle_gauge_force_link(const int dims[4], const double *U, double beta, const double c[3],
                              long k, int rho, double out[8])
 {
     field f = {make_geom(dims), (const cplx *)U};
     path p[34];
     int np = build_paths(p);
-    mat3 t = zero3();
-    for (int ip = 0; ip < np; ++ip)
-        for (int l = 0; l < p[ip].len; ++l) {
-            int dl = p[ip].d[l];
-            if (dl != rho && dl != -rho) continue;
-            long n = (dl == rho) ? k : step(&f.g, k, rho);
-            for (int j = 0; j < l; ++j) n = step(&f.g, n, -p[ip].d[j]);
-            long pos[6];
-            visit(&f.g, &p[ip], n, pos);
-            t = add(t, scale(c[p[ip].cls], staple(&f, &p[ip], pos, l, dl == rho)));
-        }
-    project(get_link(&f, k, rho), t, beta, out);
+    link_force(&f, p, np, beta, c, k, rho, out);
 }
 
 /* ---------------------------------------------------- exp map and MD (a7, a8) */

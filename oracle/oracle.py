@@ -163,7 +163,7 @@ def gauge_action_local(dims, U, beta: float, c, site: int, rho: int) -> float:
 
 
 def gauge_force(dims, U, beta: float, c) -> np.ndarray:
-    """f[V, 4, 8] = -dS/domega by the force algorithm of Sec. II."""
+    """f[V, 4, 8] = -dS/domega on every link (Eqs. 18_7_25_1 to 18_6_6_13)."""
     U = _cplx(U)
     c = np.ascontiguousarray(c, dtype=np.float64)
     V = U.shape[0]
@@ -173,7 +173,7 @@ def gauge_force(dims, U, beta: float, c) -> np.ndarray:
 
 
 def gauge_force_link(dims, U, beta: float, c, site: int, rho: int) -> np.ndarray:
-    """f[8] on one link via Eqs. 18_7_26_2/3; rho = 0..3."""
+    """f[8] on one link (start sites by Eqs. 18_7_26_2/3); rho = 0..3."""
     U = _cplx(U)
     c = np.ascontiguousarray(c, dtype=np.float64)
     out = np.zeros(8)

@@ -109,6 +109,16 @@ def battery():
             failed.append("exponential vs expm")
             break
 
+    M = rng.normal(size=(24, 1, 3, 3)) + 1j * rng.normal(size=(24, 1, 3, 3))
+    G = O.md_update_links(M, np.zeros((24, 1, 8)), 0.3)[:, 0]
+    q, r = np.linalg.qr(np.transpose(M[:, 0, :2], (0, 2, 1)))
+    d = np.diagonal(r, axis1=1, axis2=2)
+    want = np.transpose(q * (d / np.abs(d))[:, None, :], (0, 2, 1))
+    if (np.abs(G[:, :2] - want).max() > 1e-13
+            or np.abs(np.einsum("nij,nkj->nik", G, G.conj()) - np.eye(3)).max() > 1e-13
+            or np.abs(np.linalg.det(G) - 1).max() > 1e-13):
+        failed.append("reunitarisation = Gram-Schmidt (QR), in SU(3)")
+
     p = synth.momenta(DIMS, 7)
     dt = 0.07
     U1 = O.md_update_links(U, p, dt)
@@ -185,6 +195,21 @@ MUTATIONS = [
     ("link step: exponential on the right",
      "u = reunitarise(mul(exp_i_algebra(w), u));",
      "u = reunitarise(mul(u, exp_i_algebra(w)));"),
+    ("Gram-Schmidt: projection conjugated",
+     "for (int j = 0; j < 3; ++j) proj += conj(u.m[0][j]) * u.m[1][j];",
+     "for (int j = 0; j < 3; ++j) proj += u.m[0][j] * conj(u.m[1][j]);"),
+    ("Gram-Schmidt: projection added instead of subtracted",
+     "for (int j = 0; j < 3; ++j) u.m[1][j] -= proj * u.m[0][j];",
+     "for (int j = 0; j < 3; ++j) u.m[1][j] += proj * u.m[0][j];"),
+    ("Gram-Schmidt: row 1 not normalised",
+     "n1 = 1.0 / sqrt(n1);",
+     "n1 = 1.0;"),
+    ("Gram-Schmidt: row 0 not normalised",
+     "n0 = 1.0 / sqrt(n0);",
+     "n0 = 1.0;"),
+    ("Gram-Schmidt: row 2 without the complex conjugate",
+     "u.m[2][1] = conj(u.m[0][2] * u.m[1][0] - u.m[0][0] * u.m[1][2]);",
+     "u.m[2][1] = u.m[0][2] * u.m[1][0] - u.m[0][0] * u.m[1][2];"),
     ("momentum step: sign",
      "for (long i = 0; i < 8 * nlinks; ++i) p[i] += dt * f[i];",
      "for (long i = 0; i < 8 * nlinks; ++i) p[i] -= dt * f[i];"),

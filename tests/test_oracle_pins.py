@@ -215,9 +215,9 @@ def test_exponential_against_scipy():
 
 # ------------------------------------------------------------ the force
 
-def test_force_link_equals_lattice_algorithm(c1, c1_force):
-    """Eqs. 18_7_26_2/3 (start site from the link) give the same staples as
-    the lattice-wide loop of the force algorithm."""
+def test_force_link_equals_lattice_force(c1, c1_force):
+    """The single-link entry point (used for sampled parity at full size)
+    agrees with the whole-lattice one on links of every direction."""
     U, c = c1
     for n, mu in [(0, 0), (1, 1), (77, 2), (255, 3), (128, 0)]:
         np.testing.assert_allclose(O.gauge_force_link(DIMS4, U, BETA, c, n, mu),
@@ -353,6 +353,82 @@ def test_md_link_update_is_left_exponential(c1):
     for n, mu in [(0, 0), (100, 2), (255, 3)]:
         X = 1j * dt * np.einsum("a,aij->ij", p[n, mu], T)
         np.testing.assert_allclose(U2[n, mu], sla.expm(X) @ U[n, mu], atol=1e-14)
+
+
+def _gram_schmidt_by_qr(M):
+    """Rows 0 and 1 of M orthonormalised in order, from LAPACK's Householder
+    QR of the 3x2 matrix whose columns are those rows: M[:2].T = Q R, and with
+    R's diagonal made positive real (Q -> Q D, R -> D* R, |D_ii| = 1) the
+    columns of Q are the unique orthonormal pair in which row 0 is a positive
+    multiple of q0 and row 1 has a positive component along q1 -- what
+    Gram-Schmidt produces.  Returns [2, 3]."""
+    q, r = np.linalg.qr(M[:2].T)
+    d = np.diagonal(r)
+    return (q * (d / np.abs(d))[None, :]).T
+
+
+def _non_unitary_links(rng, n):
+    """Three families of links that are not in SU(3): SU(3) matrices with row
+    0 scaled and row 1 mixed with row 0, the same with row 1 scaled instead,
+    and general complex Gaussian matrices."""
+    base = H.random_su3_numpy(rng, n)
+    a = base.copy()
+    a[:, 0] *= rng.uniform(0.5, 1.5, size=(n, 1))
+    a[:, 1] += (rng.normal(size=(n, 1)) + 1j * rng.normal(size=(n, 1))) * 0.3 * a[:, 0]
+    b = base.copy()
+    b[:, 1] *= rng.uniform(0.5, 1.5, size=(n, 1))
+    b[:, 0] *= np.exp(1j * rng.uniform(0, 2 * np.pi, size=(n, 1)))
+    c = rng.normal(size=(n, 3, 3)) + 1j * rng.normal(size=(n, 3, 3))
+    return np.concatenate([a, b, c])
+
+
+def _reunitarise(M):
+    """The oracle's Gram-Schmidt alone: its link step with zero momenta
+    multiplies by exp(0) = 1 (the series of the zero matrix is exactly the
+    unit matrix) and reunitarises."""
+    U = np.ascontiguousarray(M.reshape(-1, 1, 3, 3))
+    return O.md_update_links(U, np.zeros((U.shape[0], 1, 8)), 0.3).reshape(-1, 3, 3)
+
+
+def test_reunitarise_is_gram_schmidt_on_non_unitary_links():
+    """The oracle's reunitarisation (after every link step; the paper fixes
+    none) against the definition of Gram-Schmidt, pinned without retyping it:
+    rows 0 and 1 equal LAPACK's QR factor with positive diagonal (a different
+    algorithm for the same unique pair), and the result is in SU(3),
+    U U^dag = 1 and det U = 1, which fixes row 2 given rows 0 and 1."""
+    rng = np.random.default_rng(21)
+    M = _non_unitary_links(rng, 40)
+    G = _reunitarise(M)
+    want = np.stack([_gram_schmidt_by_qr(m) for m in M])
+    assert np.abs(G[:, :2] - want).max() < 1e-14
+    eye = np.eye(3)
+    assert np.abs(np.einsum("nij,nkj->nik", G, G.conj()) - eye).max() < 1e-14
+    assert np.abs(np.linalg.det(G) - 1).max() < 1e-14
+    # already in SU(3): unchanged
+    S = H.random_su3_numpy(rng, 8)
+    assert np.abs(_reunitarise(S) - S).max() < 1e-14
+
+
+def test_reunitarise_invariances():
+    """Gram-Schmidt depends only on the ordered pair of subspaces
+    span(r0) in span(r0, r1): scaling row 0 or row 1 by a positive number and
+    adding any complex multiple of row 0 to row 1 leave the result unchanged.
+    A phase e on row 0 multiplies row 0 of the result by e and row 2 by
+    conj(e) (det U = 1), and leaves row 1 unchanged."""
+    rng = np.random.default_rng(22)
+    M = _non_unitary_links(rng, 20)
+    G = _reunitarise(M)
+    M2 = M.copy()
+    M2[:, 0] *= 2.5
+    M2[:, 1] = 0.4 * M2[:, 1] + (0.3 - 0.7j) * M2[:, 0]
+    assert np.abs(_reunitarise(M2) - G).max() < 1e-13
+    e = np.exp(0.9j)
+    M3 = M.copy()
+    M3[:, 0] *= e
+    G3 = _reunitarise(M3)
+    assert np.abs(G3[:, 0] - e * G[:, 0]).max() < 1e-13
+    assert np.abs(G3[:, 1] - G[:, 1]).max() < 1e-13
+    assert np.abs(G3[:, 2] - np.conj(e) * G[:, 2]).max() < 1e-13
 
 
 def test_kinetic_energy():
