@@ -280,20 +280,21 @@ namespace {
 // Device address of g_fixed_partials on `device`, looked up once per device
 // (the device must be current).  Host code cannot use the symbol itself: on
 // the host it names a host-side stand-in, not device memory.
-int fixed_partials_address(int device, double **out)
+cudaError_t fixed_partials_address(int device, double **out)
 {
     static std::mutex mu;
     static double *addr[64] = {nullptr};
-    if (device < 0 || device >= 64) return LQCD_ERR_CUDA;
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(mu);
     if (addr[device] == nullptr) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_fixed_partials);
-        if (e != cudaSuccess || p == nullptr) return LQCD_ERR_CUDA;
+        if (e != cudaSuccess) return e;
+        if (p == nullptr) return cudaErrorInvalidSymbol;
         addr[device] = static_cast<double *>(p);
     }
     *out = addr[device];
-    return LQCD_OK;
+    return cudaSuccess;
 }
 
 } // namespace
@@ -301,8 +302,8 @@ int fixed_partials_address(int device, double **out)
 } // namespace lqcd
 
 // Allocation-free variant of lqcd_gauge_action (declared in include/lqcd.h):
-// the same kernels, with the per-block partial sums kept in the fixed
-// library-held array above instead of a caller workspace.
+// the same argument checks and kernels, with the per-block partial sums kept
+// in the fixed library-held array above instead of a caller workspace.
 extern "C" int lqcd_gauge_action_noalloc(const lqcd_desc *desc, const void *links, double *action,
                                          void *stream)
 {
@@ -311,28 +312,20 @@ extern "C" int lqcd_gauge_action_noalloc(const lqcd_desc *desc, const void *link
         Range() { nvtxRangePushA("lqcd_gauge_action_noalloc"); }
         ~Range() { nvtxRangePop(); }
     } const trace_range;
-    if (desc == nullptr || links == nullptr || action == nullptr) return LQCD_ERR_ARG;
-    if (desc->precision != LQCD_F32 && desc->precision != LQCD_F64) return LQCD_ERR_ARG;
-    if (!std::isfinite(desc->beta) || !std::isfinite(desc->c_plaq) ||
-        !std::isfinite(desc->c_rect) || !std::isfinite(desc->c_cube))
-        return LQCD_ERR_ARG;
-    const int64_t limit = ((int64_t)1 << 62) / 72;
-    int64_t V = 1;
-    for (int i = 0; i < 4; ++i) {
-        if (desc->dims[i] < 1) return LQCD_ERR_DIMS;
-        V *= desc->dims[i];
-        if (V > limit) return LQCD_ERR_DIMS;
-    }
-    if (((uintptr_t)links & 15u) != 0) return LQCD_ERR_ALIGN;
+    int s = lqcd::check_desc(desc);
+    if (s) return s;
+    if ((s = lqcd::check_ptrs({links}))) return s;
+    if (action == nullptr) return LQCD_ERR_ARG;
     if (((uintptr_t)action & 7u) != 0) return LQCD_ERR_ALIGN;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return LQCD_ERR_CUDA;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return lqcd::cuda_status(e);
     const int blocks = lqcd::reduction_blocks(dev);
-    if (blocks <= 0) return LQCD_ERR_CUDA;
+    if (blocks <= 0) return lqcd::cuda_status(cudaErrorInvalidDevice);
     if (blocks > lqcd::kFixedPartials) return LQCD_ERR_CAPACITY;
     double *partials = nullptr;
-    const int st = lqcd::fixed_partials_address(dev, &partials);
-    if (st != LQCD_OK) return st;
+    e = lqcd::fixed_partials_address(dev, &partials);
+    if (e != cudaSuccess) return lqcd::cuda_status(e);
     lqcd::ReduceArgs a{};
     for (int i = 0; i < 4; ++i) a.dims[i] = desc->dims[i];
     a.precision = desc->precision;
@@ -344,7 +337,5 @@ extern "C" int lqcd_gauge_action_noalloc(const lqcd_desc *desc, const void *link
     a.partials = partials;
     a.blocks = blocks;
     a.out = action;
-    return lqcd::launch_action(a, static_cast<cudaStream_t>(stream)) == cudaSuccess
-               ? LQCD_OK
-               : LQCD_ERR_CUDA;
+    return lqcd::cuda_status(lqcd::launch_action(a, static_cast<cudaStream_t>(stream)));
 }

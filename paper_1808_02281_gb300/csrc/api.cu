@@ -21,6 +21,10 @@ struct TraceRange {
 
 thread_local int g_last_cuda_error = 0;
 
+} // namespace
+
+namespace lqcd {
+
 int cuda_status(cudaError_t e)
 {
     if (e == cudaSuccess) return LQCD_OK;
@@ -58,6 +62,15 @@ int check_ptrs(std::initializer_list<const void *> ps)
     }
     return LQCD_OK;
 }
+
+} // namespace lqcd
+
+namespace {
+
+using lqcd::aligned16;
+using lqcd::check_desc;
+using lqcd::check_ptrs;
+using lqcd::cuda_status;
 
 void copy_dims(int out[4], const lqcd_desc *d)
 {

@@ -4,11 +4,22 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <initializer_list>
 #include <cuda_runtime.h>
 
 #include "../../include/lqcd.h"
 
 namespace lqcd {
+
+// Argument checks shared by every entry point (api.cu): the descriptor
+// (precision, algorithm, finite parameters, extents >= 1 and addressable),
+// and device pointers (non-NULL: else LQCD_ERR_ARG; 16-byte aligned: else
+// LQCD_ERR_ALIGN).  cuda_status maps a CUDA error to LQCD_ERR_CUDA and keeps
+// it for lqcd_last_cuda_error() on the calling thread.
+int check_desc(const lqcd_desc *d);
+int check_ptrs(std::initializer_list<const void *> ps);
+bool aligned16(const void *p);
+int cuda_status(cudaError_t e);
 
 // One staple of the path kernel: cls (0 plaquette, 1 rectangle, 2 cube),
 // len (3 or 5) signed directions +-(mu+1), walked from k + rho.
