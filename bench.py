@@ -10,10 +10,14 @@ Inputs (403 MB of links, 268 MB of momenta, 268 MB of force) are larger
 than the 129 MB L2, so no flush is needed between steps.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--force-variant V]
+                       [--force-variant V] [--profile-force WORKLOAD]
 N > 1 runs as independent replicas, one lattice per rank (the path has no
 exchange step on one lattice per GPU); value = links of all ranks / max time.
 --impl reference times the FP64 CPU oracle on the host cores instead.
+--profile-force WORKLOAD runs only W + K FP32 force calls (the staple-field
+force with the fused momentum step and action) on that workload (a key of
+synth.WORKLOADS, e.g. 16^3x32) and prints their mean time: the small case
+that profiler captures run.
 """
 from __future__ import annotations
 
@@ -42,6 +46,18 @@ DT = 0.05
 # projection): 36.9 kflop; compulsory bytes: FP32 12-real link read (48 B) +
 # 8-real force write (32 B).
 FLOP_PER_LINK_FORCE = 36.9e3
+# What the staple-field force executes per link (FP32, full staple planes,
+# FMA = 2 flops; a compact link's row 2 rebuild = 42 flops; a product of two
+# SU(3) matrices with its third row rebuilt from its first two and
+# accumulated = 144 + 42 + 36 = 222; a plain accumulated product = 216):
+#   staple planes: 6 staples per link, each two link rebuilds (84), rows 0
+#     and 1 of the first product (132), rows 0 and 1 of the second (144) and
+#     the staple's third row (42): 2412;
+#   force pass: plaquette and rectangle chains 6 x (18 + 222 + 216) = 2736,
+#     their two link products and scalings 552, the action's trace 78,
+#     six d-terms of 5 x 222 + 216 + 2 x 42 = 1410 each (8460), U t and the
+#     projection, momentum step and action share (~282): 12108.
+EXECUTED_FLOP_PER_LINK_FORCE = 2412 + 12108
 BYTES_PER_LINK_FORCE = {"f32": 80, "f64": 160}
 # streaming kernels, compulsory bytes per link
 BYTES_MOM_UPDATE = {"f32": 96, "f64": 192}     # read p, read f, write p
@@ -56,6 +72,8 @@ CPU_SAMPLE_DIMS = (12, 12, 12, 12)
 # momentum step reads per link its link (12 R), a quarter of a site's X and Y
 # (12 R) and the momenta (8 R), and writes the momenta (8 R).
 WILSON_KAPPA = 0.1315
+# thermalising FP32 trajectories before the same-start dH comparison
+DH_THERM = 30
 WILSON_REALS_PER_SITE_DSLASH = 96
 WILSON_REALS_PER_LINK_FORCE = 40
 
@@ -83,18 +101,21 @@ def _source_digest() -> str:
     return h.hexdigest()[:16]
 
 
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "force_traffic_f32_32x32x32x64.json")
+
+
 def _recorded_traffic():
-    """DRAM bytes per force launch from the committed ncu summary, if it was
-    taken on the current force kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", "force_staple_fields_f32_32x32x32x64.md")
+    """DRAM bytes (read + write) per force call at the bench workload from the
+    machine-readable record written beside the ncu summary, if it was taken
+    on the current force kernel source (same digest); else None."""
     try:
-        text = open(path).read()
-    except OSError:
+        with open(TRAFFIC_RECORD) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
         return None
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s+source_sha256:\s*([0-9a-f]+)", text)
-    if not m or m.group(2) != _source_digest():
+    if rec.get("source_digest") != _source_digest():
         return None
-    return float(m.group(1))
+    return float(rec["traffic_bytes_per_call"])
 
 
 # ----------------------------------------------------------------- clocks
@@ -394,71 +415,95 @@ def run_ours(args):
     ms64 = max_over_ranks(ms64)
 
     # end to end through the public API with host buffers: every step's links
-    # and momenta are copied from pinned host memory and the step's action is
-    # copied back to pinned host memory; as a user of the API would pipeline
-    # it, the copy of step k+1's inputs (copy stream) overlaps step k's
-    # kernels (compute stream), with two device buffer sets
+    # and momenta are copied from pinned host memory, and the step's results
+    # -- the updated links, the updated momenta and the action -- are copied
+    # back to pinned host memory.  As a user of the API would pipeline it,
+    # three device buffer sets rotate: while step k computes (compute
+    # stream), step k+1's inputs are copied in (input stream) and step k-1's
+    # results are copied out (output stream).
     lat, U0, mom0, force, S0, ws = make("f32")
     U_host = U0.detach().to("cpu").pin_memory()
     mom_host = mom0.detach().to("cpu").pin_memory()
+    U_out = torch.empty_like(U_host).pin_memory()
+    mom_out = torch.empty_like(mom_host).pin_memory()
     K_e2e = max(3, args.steps)
     S_host = torch.empty(K_e2e, dtype=torch.float64).pin_memory()
     h2d = U_host.numel() * U_host.element_size() + mom_host.numel() * mom_host.element_size()
-    d2h = 8
-    Ub = [U0, torch.empty_like(U0)]
-    mb = [mom0, torch.empty_like(mom0)]
-    Sb = [S0, torch.empty_like(S0)]
-    copy_stream = torch.cuda.Stream(dev)
-    copied = [torch.cuda.Event(), torch.cuda.Event()]
-    done = [torch.cuda.Event(), torch.cuda.Event()]
+    d2h = h2d + 8
+    NB = 3
+    Ub = [U0] + [torch.empty_like(U0) for _ in range(NB - 1)]
+    mb = [mom0] + [torch.empty_like(mom0) for _ in range(NB - 1)]
+    Sb = [S0] + [torch.empty_like(S0) for _ in range(NB - 1)]
+    in_stream, out_stream = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    copied = [torch.cuda.Event() for _ in range(NB)]   # inputs of buffer b on the device
+    computed = [torch.cuda.Event() for _ in range(NB)]  # step on buffer b done
+    drained = [torch.cuda.Event() for _ in range(NB)]  # results of buffer b on the host
+
+    def put(b, used):
+        if used[b]:
+            in_stream.wait_event(drained[b])
+        with torch.cuda.stream(in_stream):
+            Ub[b].copy_(U_host, non_blocking=True)
+            mb[b].copy_(mom_host, non_blocking=True)
+            copied[b].record(in_stream)
 
     def e2e_run(K):
-        used = [False, False]
-        with torch.cuda.stream(copy_stream):
-            Ub[0].copy_(U_host, non_blocking=True)
-            mb[0].copy_(mom_host, non_blocking=True)
-            copied[0].record(copy_stream)
+        used = [False] * NB
+        put(0, used)
         for k in range(K):
-            b = k % 2
+            b = k % NB
             if k + 1 < K:
-                nb = 1 - b
-                if used[nb]:
-                    copy_stream.wait_event(done[nb])
-                with torch.cuda.stream(copy_stream):
-                    Ub[nb].copy_(U_host, non_blocking=True)
-                    mb[nb].copy_(mom_host, non_blocking=True)
-                    copied[nb].record(copy_stream)
+                put((k + 1) % NB, used)
             stream.wait_event(copied[b])
             step(lat, Ub[b], mb[b], force, Sb[b], ws)
-            S_host[k].copy_(Sb[b], non_blocking=True)
-            done[b].record(stream)
+            computed[b].record(stream)
+            out_stream.wait_event(computed[b])
+            with torch.cuda.stream(out_stream):
+                U_out.copy_(Ub[b], non_blocking=True)
+                mom_out.copy_(mb[b], non_blocking=True)
+                S_host[k].copy_(Sb[b], non_blocking=True)
+                drained[b].record(out_stream)
             used[b] = True
+        stream.wait_stream(out_stream)
 
     e2e_run(2)
     torch.cuda.synchronize(dev)
     barrier()
     e_start, e_stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e_start.record(stream)
-    copy_stream.wait_event(e_start)
+    in_stream.wait_event(e_start)
+    out_stream.wait_event(e_start)
     e2e_run(K_e2e)
     e_stop.record(stream)
     torch.cuda.synchronize(dev)
     assert all(np.isfinite(S_host.numpy())), "non-finite action in the end-to-end steps"
+    assert bool(torch.isfinite(U_out).all()) and bool(torch.isfinite(mom_out).all())
     e_ms = max_over_ranks(e_start.elapsed_time(e_stop))
     del Ub, mb, Sb, U0, mom0, force, S0, ws
     torch.cuda.empty_cache()
     e2e_value = weak_scaling_value(nlinks, world, K_e2e, e_ms)
 
-    # dH of one Omelyan trajectory (tau 0.5, dt 0.05) from the same draws in
-    # FP32 and FP64, H = K + S in FP64 (FP64 action of the FP32-stored links)
+    # dH of one Omelyan trajectory (tau 0.5, dt 0.05) in FP32 and in FP64
+    # from the same state: the synthetic start thermalised by FP32
+    # trajectories, then the same links and momenta in both precisions (FP32
+    # values promoted exactly); H = K + S in FP64 in both, so the difference
+    # of the two dH is the error of the FP32 arithmetic alone
     from paper_1808_02281_gb300 import hmc
-    dh = {"integrator": "omelyan", "tau": 0.5, "dt": 0.05, "dims": list(dims)}
-    for prec in ("f32", "f64"):
-        st = hmc.initial_state(dims, prec, w["sigma"], w["u0"], w["beta"], seed)
-        dh[prec] = hmc.trajectory(st, 0.5, 0.05, "omelyan", action_precision="f64")
-        del st
-        torch.cuda.empty_cache()
-    dh["abs_err_f32"] = abs(dh["f32"] - dh["f64"])
+    recs = list(hmc.same_start_study(dims, 0.5, [0.05], "omelyan", seed, n_therm=DH_THERM,
+                                     therm_tau=0.5, therm_dt=0.025, sigma=w["sigma"],
+                                     u0=w["u0"], beta=w["beta"]))
+    therm = [r for r in recs if r["phase"] == "thermalise"]
+    study = [r for r in recs if r["phase"] == "study"][0]
+    dh = {"integrator": "omelyan", "tau": 0.5, "dt": 0.05, "dims": list(dims),
+          "start": f"w ~ N(0, {w['sigma']}^2) links thermalised by {DH_THERM} FP32 trajectories "
+                   "(tau 0.5, dt 0.025, momentum refresh, no accept/reject), reunitarised in "
+                   "FP64; then the same values in FP32 and FP64",
+          "thermalise_action": [r["action"] for r in therm],
+          "f32": study["dH_f32"], "f64": study["dH_f64"], "abs_err_f32": study["abs_diff"],
+          "f32_with_f32_action": study["dH_f32_f32action"], "H0": study["H0"],
+          "same_H0": study["H0_equal"],
+          "seconds_f32": study["seconds_f32"], "seconds_f64": study["seconds_f64"]}
+    torch.cuda.empty_cache()
     # the same FP32 trajectory captured as one CUDA graph, replayed
     st = hmc.initial_state(dims, "f32", w["sigma"], w["u0"], w["beta"], seed)
     g_traj = hmc.GraphTrajectory(st, 0.05, 10, "omelyan")
@@ -580,6 +625,7 @@ def run_ours(args):
 
     force_ms = per["force"]
     achieved_tflops = FLOP_PER_LINK_FORCE * nlinks / (force_ms / 1e3) / 1e12
+    executed_tflops = EXECUTED_FLOP_PER_LINK_FORCE * nlinks / (force_ms / 1e3) / 1e12
     roofline = {
         "bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
         "frac": achieved_tflops / FP32_PEAK_TFLOPS, "traffic": _recorded_traffic(),
@@ -587,10 +633,15 @@ def run_ours(args):
                   "(one lqcd_md_force_step call, momentum step and action fused)",
         "units_per_launch": nlinks,
         "algorithmic_flop_per_unit": FLOP_PER_LINK_FORCE,
+        "executed_flop_per_unit": EXECUTED_FLOP_PER_LINK_FORCE,
+        "executed_achieved": executed_tflops,
+        "executed_frac": executed_tflops / FP32_PEAK_TFLOPS,
+        "algorithmic_bytes_per_unit": BYTES_PER_LINK_FORCE["f32"],
         "peak_note": "FP32 pipe: 152 SMs x 128 lanes x 2 flop x 2.070 GHz (unit counts and "
-                     "maximum clock); algorithmic flops count the literal 180-product "
-                     "algorithm, the staple-field force executes 63 products per link, "
-                     "so frac can exceed the executed-FMA utilisation by up to 2.9x",
+                     "maximum clock); 'achieved'/'frac' count the literal 180-product "
+                     "algorithm's flops, 'executed_*' the flops the staple-field force "
+                     "executes (63 SU(3) products per link): executed_frac is the FP32-pipe "
+                     "utilisation",
         "hbm_frac_of_" + peak_kind: BYTES_PER_LINK_FORCE["f32"] * nlinks / (force_ms / 1e3) / 1e9
         / hbm_peak,
     }
@@ -643,12 +694,48 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "Glink/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": K_e2e,
-                "pipelining": "inputs of step k+1 copied on a second stream during step k"},
+                "results_copied_back": "updated links and momenta, and the action",
+                "pipelining": "three device buffer sets: step k+1's inputs copied in and step "
+                              "k-1's results copied out on two copy streams during step k"},
         "gpu_launches": n_launch,
         "clocks": clocks,
     }
     print(json.dumps(out))
     ctx.close()
+    return 0
+
+
+def run_profile_force(args):
+    """W + K FP32 force calls (staple planes, force pass with the fused
+    momentum step and action) on one workload, for profiler captures of a
+    small case; prints the mean time of the K timed calls."""
+    import torch
+
+    from paper_1808_02281_gb300 import build as B
+    from paper_1808_02281_gb300 import lqcd, synth
+
+    B.build()
+    w = synth.WORKLOADS[args.profile_force]
+    dims = w["dims"]
+    lat = lqcd.Lattice.symanzik(dims, w["beta"], w["u0"], "f32")
+    U = lqcd.links_from_omega(lat, lqcd.algebra_to_device(lat, synth.omega(dims, w["sigma"], w["seed"])))
+    mom = lqcd.algebra_to_device(lat, synth.momenta(dims, seed=1000 + w["seed"]))
+    S = torch.empty((), dtype=torch.float64, device="cuda")
+    ws = lqcd.make_workspace(lat)
+    if args.force_variant >= 0:
+        lqcd.set_force_variant(lat, args.force_variant)
+    for _ in range(args.warmup):
+        lqcd.md_force_step(lat, U, mom=mom, dt=DT, action=S, workspace=ws)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        lqcd.md_force_step(lat, U, mom=mom, dt=DT, action=S, workspace=ws)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    print(json.dumps({"profile_force": args.profile_force, "variant": lqcd.get_force_variant(lat),
+                      "links": 4 * lat.V, "force_ms": ms, "action": float(S.item())}))
     return 0
 
 
@@ -659,11 +746,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--force-variant", type=int, default=-1,
-                    help="fix the staple-field force schedule (0..6) instead of autotuning it "
+                    help="fix the staple-field force schedule (0..7) instead of autotuning it "
                          "at set-up; -1 (default) autotunes")
+    ap.add_argument("--profile-force", default=None, metavar="WORKLOAD",
+                    help="only time FP32 force calls on this workload (profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.profile_force:
+        return run_profile_force(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -145,8 +145,9 @@ LQCD_API int lqcd_md_force_step(const lqcd_desc *desc, const void *links, void *
                        void *stream);
 
 /* Schedules of the force kernels.  An algorithm may come in several
- * variants that compute the same result with a different traversal or
- * pipelining (LQCD_FORCE_STAPLE_FIELDS / AUTO: 4; the others: 1).  The choice
+ * variants that compute the same result with a different traversal,
+ * storage or register budget (LQCD_FORCE_STAPLE_FIELDS / AUTO: 7; the
+ * others: 1).  The choice
  * is process-wide per precision.
  *   lqcd_force_variant_count: number of variants for desc->force_algo.
  *   lqcd_get_force_variant / lqcd_set_force_variant: the current choice;
@@ -360,9 +361,11 @@ LQCD_API size_t lqcd_fma_rate_scratch_bytes(void);
 /* Bytes of device workspace that this descriptor needs on the current
  * device: the staple planes and action partials of the staple-field force
  * (force_algo STAPLE_FIELDS or AUTO; 24 SU(3) planes per site -- 1728 bytes
- * in FP32, 3456 in FP64, room for either storage form -- plus one double per
- * 32 sites) and the partial sums of lqcd_gauge_action / lqcd_kinetic_energy
- * (0 on a bad descriptor). */
+ * in FP32, 3456 in FP64, room for either storage form, with V rounded up to
+ * a multiple of 32 -- plus one double per 32 sites) and the partial sums of
+ * lqcd_gauge_action / lqcd_kinetic_energy (0 on a bad descriptor).  The
+ * staple-field algorithm indexes sites with 32-bit integers: for V >= 2^31
+ * it returns LQCD_ERR_DIMS (AUTO then takes the factored algorithm). */
 LQCD_API size_t lqcd_workspace_bytes(const lqcd_desc *desc);
 
 /* Human-readable text of a status code (static storage). */

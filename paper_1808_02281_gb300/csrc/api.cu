@@ -113,7 +113,9 @@ int run_force(const lqcd_desc *desc, const void *links, void *force, void *mom, 
               double *action, void *workspace, size_t workspace_bytes, void *stream)
 {
     int algo = desc->force_algo;
-    const bool sf_ok = workspace_fits(workspace, workspace_bytes, staple_workspace_bytes(desc));
+    const bool sf_dims = lqcd::staple_fields_supported(desc->dims);
+    if (algo == LQCD_FORCE_STAPLE_FIELDS && !sf_dims) return LQCD_ERR_DIMS;
+    const bool sf_ok = sf_dims && workspace_fits(workspace, workspace_bytes, staple_workspace_bytes(desc));
     if (algo == LQCD_FORCE_STAPLE_FIELDS && !sf_ok) return LQCD_ERR_WORKSPACE;
     if (algo == LQCD_FORCE_AUTO) algo = sf_ok ? LQCD_FORCE_STAPLE_FIELDS : LQCD_FORCE_FACTORED;
     int red_blocks = 0;
@@ -279,9 +281,11 @@ int lqcd_md_force_step_batched(const lqcd_desc *desc, int n, const lqcd_lattice_
     if (desc->force_algo != LQCD_FORCE_AUTO && desc->force_algo != LQCD_FORCE_STAPLE_FIELDS)
         return LQCD_ERR_UNSUPPORTED;
     if (!std::isfinite(dt)) return LQCD_ERR_ARG;
-    for (int c = 0; c < n; ++c)
+    for (int c = 0; c < n; ++c) {
         if (lats[c].force == nullptr && lats[c].mom == nullptr && lats[c].action == nullptr)
             return LQCD_ERR_ARG;
+        if (!lqcd::staple_fields_supported(lats[c].dims)) return LQCD_ERR_DIMS;
+    }
     if (!workspace_fits(workspace, workspace_bytes, batch_workspace_bytes(desc, n, lats)))
         return LQCD_ERR_WORKSPACE;
     lqcd::SfLattice items[LQCD_MAX_BATCH];
@@ -375,6 +379,7 @@ int lqcd_autotune_force(const lqcd_desc *desc, const void *links, void *force, v
         if (best) *best = 0;
         return LQCD_OK;
     }
+    if (!lqcd::staple_fields_supported(desc->dims)) return LQCD_ERR_DIMS;
     if (!workspace_fits(workspace, workspace_bytes, staple_workspace_bytes(desc)))
         return LQCD_ERR_WORKSPACE;
     lqcd_desc d = *desc;

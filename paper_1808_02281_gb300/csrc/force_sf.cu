@@ -70,94 +70,204 @@ template <typename R> __device__ __forceinline__ R scalar(const KernelScalars &s
 }
 
 // Storage of the 24 staple planes: compact (rows 0 and 1, 12 reals, the
-// third row rebuilt on load, as for links) or full (all 18 reals, nothing
-// rebuilt).  Full planes hold 18/W whole 16-byte lanes per plane, plane P's
-// lane q at ((P*NW + q)*V + n); in FP32 the last two reals of every plane go
-// to a float2 region after all 24*4 lanes, at (P*V + n): 72 bytes per staple
-// instead of 80, with every load and store still 16- or 8-byte aligned.
+// third row rebuilt on load, in the link layout) or full (all 18 reals,
+// nothing rebuilt).  Full planes are cut into blocks of 32 consecutive sites:
+// inside a block, 16-byte lane q (q < NW = 18/W) of the staple of site s is
+// at q*512 + s*16 bytes, and in FP32 its last two reals at NW*512 + s*8 --
+// 72 bytes per staple in FP32, 144 in FP64, every access 16- or 8-byte
+// aligned, and the lanes of one staple a constant 512 bytes apart, so that a
+// staple costs one address computation (plus one for the FP32 tail) however
+// many lanes it has.  Plane P starts at P * plane_bytes, plane_bytes = the
+// 32-site blocks of the lattice (V rounded up to 32) times the block size.
 // Pass A writes them with evict-first stores: the 3.6 GB (at 32^3x64) would
 // otherwise push the links that pass A re-reads out of L2.
 constexpr int kStaplePlanes = 24;
 
-template <typename R, bool FULL> struct Staples {
+template <typename R> struct FullBlock {
     using V4 = typename Vec<R>::type;
     static constexpr int W = Vec<R>::W;
-    static constexpr int NW = FULL ? 18 / W : 12 / W; // whole lanes per plane
-    static constexpr int TAIL = FULL ? 18 - NW * W : 0; // reals in the float2 region (FP32 full: 2)
-    static_assert(NW * W + TAIL == (FULL ? 18 : 12), "a plane holds 12 (compact) or 18 reals");
+    static constexpr int NW = 18 / W;        // whole 16-byte lanes per staple
+    static constexpr int TAIL = 18 - NW * W; // reals in the FP32 tail (2)
+    static constexpr int LANE = 32 * 16;     // bytes of one lane of a block
+    static constexpr int BYTES = NW * LANE + TAIL * (int)sizeof(R) * 32;
+    static_assert(NW * W + TAIL == 18, "a full staple holds 18 reals");
+};
 
-    static __device__ __forceinline__ const float2 *tail(const R *sf, int64_t V)
+size_t full_plane_bytes(int64_t V, int precision)
+{
+    const size_t blk = precision == LQCD_F64 ? FullBlock<double>::BYTES : FullBlock<float>::BYTES;
+    return (size_t)((V + 31) / 32) * blk;
+}
+
+template <typename R, bool FULL> struct Planes;
+
+// Compact planes: plane P is laid out like the links of direction P.
+template <typename R> struct Planes<R, false> {
+    R *sf;
+    int64_t V;
+    using Ref = int;
+
+    __device__ __forceinline__ Ref at(int n) const { return n; }
+
+    template <bool COH = false> __device__ __forceinline__ Mat<R> load(Ref n, int plane) const
     {
-        return reinterpret_cast<const float2 *>(sf + (int64_t)kStaplePlanes * NW * W * V);
+        static_assert(!COH, "compact planes are only read-only fields");
+        return load_link(sf, V, plane, n);
     }
 
-    static __device__ __forceinline__ Mat<R> load(const R *__restrict__ sf, int64_t V, int plane,
-                                                  int64_t n)
+    template <bool STREAM = true> __device__ __forceinline__ void store(Ref n, int plane, const Mat<R> &u) const
     {
-        if constexpr (!FULL) {
-            return load_link(sf, V, plane, n);
-        } else {
-            const V4 *p = reinterpret_cast<const V4 *>(sf) + (int64_t)plane * NW * V + n;
-            R r[18];
+        store_link(sf, V, plane, n, u);
+    }
+};
+
+template <typename R> struct Planes<R, true> {
+    using B = FullBlock<R>;
+    using V4 = typename B::V4;
+    char *base;          // plane 0
+    int64_t plane_bytes;
+
+    // The lane-0 and tail addresses of site n in plane 0.
+    struct Ref {
+        char *p;
+        char *t;
+    };
+
+    __device__ __forceinline__ Ref at(int n) const
+    {
+        char *b = base + (int64_t)(n >> 5) * B::BYTES;
+        const int s = n & 31;
+        return Ref{b + s * 16, b + B::NW * B::LANE + s * 8};
+    }
+
+    // COH: a coherent load (planes written by other blocks of the same
+    // launch, read after an acquire), else the read-only path.
+    template <bool COH = false> __device__ __forceinline__ Mat<R> load(const Ref &r, int plane) const
+    {
+        const int64_t off = (int64_t)plane * plane_bytes;
+        const V4 *p = reinterpret_cast<const V4 *>(r.p + off);
+        R x[18];
 #pragma unroll
-            for (int q = 0; q < NW; ++q) {
-                const V4 v = __ldg(p + q * V);
-                if constexpr (W == 4) {
-                    r[4 * q + 0] = v.x;
-                    r[4 * q + 1] = v.y;
-                    r[4 * q + 2] = v.z;
-                    r[4 * q + 3] = v.w;
-                } else {
-                    r[2 * q + 0] = v.x;
-                    r[2 * q + 1] = v.y;
-                }
+        for (int q = 0; q < B::NW; ++q) {
+            const V4 v = COH ? __ldca(p + q * (B::LANE / 16)) : __ldg(p + q * (B::LANE / 16));
+            if constexpr (B::W == 4) {
+                x[4 * q + 0] = v.x;
+                x[4 * q + 1] = v.y;
+                x[4 * q + 2] = v.z;
+                x[4 * q + 3] = v.w;
+            } else {
+                x[2 * q + 0] = v.x;
+                x[2 * q + 1] = v.y;
             }
-            if constexpr (TAIL == 2) {
-                const float2 t = __ldg(tail(sf, V) + (int64_t)plane * V + n);
-                r[16] = t.x;
-                r[17] = t.y;
-            }
-            Mat<R> u;
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    u.re[i][j] = r[2 * (3 * i + j)];
-                    u.im[i][j] = r[2 * (3 * i + j) + 1];
-                }
-            return u;
         }
+        if constexpr (B::TAIL == 2) {
+            const float2 *tp = reinterpret_cast<const float2 *>(r.t + off);
+            const float2 t = COH ? __ldca(tp) : __ldg(tp);
+            x[16] = t.x;
+            x[17] = t.y;
+        }
+        Mat<R> u;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                u.re[i][j] = x[2 * (3 * i + j)];
+                u.im[i][j] = x[2 * (3 * i + j) + 1];
+            }
+        return u;
     }
 
-    static __device__ __forceinline__ void store(R *__restrict__ sf, int64_t V, int plane, int64_t n,
-                                                 const Mat<R> &u)
+    // STREAM: evict-first stores (a field read back after the pass), else
+    // plain stores (data that should stay in L2).
+    template <bool STREAM = true>
+    __device__ __forceinline__ void store(const Ref &r, int plane, const Mat<R> &u) const
     {
-        if constexpr (!FULL) {
-            store_link(sf, V, plane, n, u);
-        } else {
-            V4 *p = reinterpret_cast<V4 *>(sf) + (int64_t)plane * NW * V + n;
-            R r[18];
+        const int64_t off = (int64_t)plane * plane_bytes;
+        V4 *p = reinterpret_cast<V4 *>(r.p + off);
+        R x[18];
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    r[2 * (3 * i + j)] = u.re[i][j];
-                    r[2 * (3 * i + j) + 1] = u.im[i][j];
-                }
-#pragma unroll
-            for (int q = 0; q < NW; ++q) {
-                V4 v;
-                if constexpr (W == 4) v = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
-                else v = make_double2(r[2 * q], r[2 * q + 1]);
-                __stcs(p + q * V, v);
+            for (int j = 0; j < 3; ++j) {
+                x[2 * (3 * i + j)] = u.re[i][j];
+                x[2 * (3 * i + j) + 1] = u.im[i][j];
             }
-            if constexpr (TAIL == 2) {
-                float2 *t = const_cast<float2 *>(tail(sf, V)) + (int64_t)plane * V + n;
-                __stcs(t, make_float2(r[16], r[17]));
-            }
+#pragma unroll
+        for (int q = 0; q < B::NW; ++q) {
+            V4 v;
+            if constexpr (B::W == 4) v = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+            else v = make_double2(x[2 * q], x[2 * q + 1]);
+            if constexpr (STREAM) __stcs(p + q * (B::LANE / 16), v);
+            else p[q * (B::LANE / 16)] = v;
+        }
+        if constexpr (B::TAIL == 2) {
+            float2 *tp = reinterpret_cast<float2 *>(r.t + off);
+            if constexpr (STREAM) __stcs(tp, make_float2(x[16], x[17]));
+            else *tp = make_float2(x[16], x[17]);
         }
     }
 };
+
+template <typename R, bool FULL> __device__ __forceinline__ Planes<R, FULL> planes_of(const SfLattice &L)
+{
+    if constexpr (FULL) {
+        return Planes<R, true>{static_cast<char *>(L.staples), L.plane_bytes};
+    } else {
+        const int64_t V = (int64_t)L.dims[0] * L.dims[1] * L.dims[2] * L.dims[3];
+        return Planes<R, false>{static_cast<R *>(L.staples), V};
+    }
+}
+
+// Lattice geometry in 32-bit arithmetic: the staple-field algorithm runs only
+// for V < 2^31 sites (its workspace, 1728 bytes a site in FP32, could not
+// hold more), so site indices and neighbour offsets fit an int.
+struct G32 {
+    int L0, L1, L2, L3;
+    int s1, s2, s3, V;
+};
+
+__device__ __forceinline__ G32 make_g32(const int dims[4])
+{
+    G32 g;
+    g.L0 = dims[0];
+    g.L1 = dims[1];
+    g.L2 = dims[2];
+    g.L3 = dims[3];
+    g.s1 = dims[0];
+    g.s2 = g.s1 * dims[1];
+    g.s3 = g.s2 * dims[2];
+    g.V = g.s3 * dims[3];
+    return g;
+}
+
+__device__ __forceinline__ Coord coord32(const G32 &g, int n)
+{
+    Coord x;
+    x.c3 = n / g.s3;
+    int r = n - x.c3 * g.s3;
+    x.c2 = r / g.s2;
+    r -= x.c2 * g.s2;
+    x.c1 = r / g.s1;
+    x.c0 = r - x.c1 * g.s1;
+    return x;
+}
+
+__device__ __forceinline__ int index32(const G32 &g, const Coord &x)
+{
+    return x.c0 + g.s1 * x.c1 + g.s2 * x.c2 + g.s3 * x.c3;
+}
+
+// Index offset of the step s * hat(mu) (s = +-1) from a site with
+// coordinates x, periodic (the direction picked by a select chain, so that
+// nothing is indexed at run time in per-thread storage).
+__device__ __forceinline__ int step32(const G32 &g, const Coord &x, int mu, int s)
+{
+    const int L = pick(mu, g.L0, g.L1, g.L2, g.L3);
+    const int c = pick(mu, x.c0, x.c1, x.c2, x.c3);
+    const int st = pick(mu, 1, g.s1, g.s2, g.s3);
+    if (s > 0) return c + 1 == L ? (1 - L) * st : st;
+    return c == 0 ? (L - 1) * st : -st;
+}
 
 // Traversal order of pass B: the lattice is cut into spatial blocks of
 // bx x by x bz sites that run over all t; blocks one after the other, inside
@@ -168,10 +278,10 @@ template <typename R, bool FULL> struct Staples {
 struct Sweep {
     int bx, by, bz, mx, my, mz;
     int nbx, nby, nmx, nmy, mvol;
-    int64_t slice, vol; // sites per block slice and per block
+    int slice, vol; // sites per block slice and per block
 };
 
-__device__ __forceinline__ Sweep make_sweep(const SfLattice &L, const Geom &g)
+__device__ __forceinline__ Sweep make_sweep(const SfLattice &L, const G32 &g)
 {
     Sweep s;
     s.bx = L.sweep[0];
@@ -185,25 +295,25 @@ __device__ __forceinline__ Sweep make_sweep(const SfLattice &L, const Geom &g)
     s.nmx = s.bx / s.mx;
     s.nmy = s.by / s.my;
     s.mvol = s.mx * s.my * s.mz;
-    s.slice = (int64_t)s.bx * s.by * s.bz;
+    s.slice = s.bx * s.by * s.bz;
     s.vol = s.slice * g.L3;
     return s;
 }
 
-__device__ __forceinline__ Coord swept_site(const Sweep &s, int64_t j)
+__device__ __forceinline__ Coord swept_site(const Sweep &s, int j)
 {
-    const int64_t blk = j / s.vol;
-    const int64_t r = j - blk * s.vol;
+    const int blk = j / s.vol;
+    const int r = j - blk * s.vol;
     Coord c;
-    c.c3 = (int)(r / s.slice);
-    const int r2 = (int)(r - c.c3 * s.slice);
+    c.c3 = r / s.slice;
+    const int r2 = r - c.c3 * s.slice;
     const int mt = r2 / s.mvol, w = r2 - mt * s.mvol;
     const int xin = w % s.mx, yin = (w / s.mx) % s.my, zin = w / (s.mx * s.my);
     const int mxi = mt % s.nmx, myi = (mt / s.nmx) % s.nmy, mzi = mt / (s.nmx * s.nmy);
-    const int bxi = (int)(blk % s.nbx);
-    const int64_t q = blk / s.nbx;
-    const int byi = (int)(q % s.nby);
-    const int bzi = (int)(q / s.nby);
+    const int bxi = blk % s.nbx;
+    const int q = blk / s.nbx;
+    const int byi = q % s.nby;
+    const int bzi = q / s.nby;
     c.c0 = bxi * s.bx + mxi * s.mx + xin;
     c.c1 = byi * s.by + myi * s.my + yin;
     c.c2 = bzi * s.bz + mzi * s.mz + zin;
@@ -254,43 +364,52 @@ __device__ __forceinline__ int batch_entry(const SfBatch &B, int64_t vb)
 
 // ---------------------------------------------------------------- pass A
 
-// The 24 staples of the 32 sites of virtual block vb: thread = (site, mu).
-template <typename R, bool FULL>
-__device__ __forceinline__ void staples_block(const SfLattice &L, const Geom &g, int64_t vb)
+// The six staples S^{(mu)}_b, b = +-nu (nu != mu), of the link (x, mu), x
+// at coordinates c; stored at staple index sx of sf.
+template <typename R, bool FULL, bool STREAM>
+__device__ __forceinline__ void site_staples(const R *__restrict__ links, const G32 &g, const Coord &c,
+                                             int x, int mu, const Planes<R, FULL> &sf, int sx)
 {
-    const R *__restrict__ links = static_cast<const R *>(L.links);
-    R *__restrict__ sf = static_cast<R *>(L.staples);
-    const int mu = (int)(threadIdx.x >> 5);
-    const int64_t x = vb * 32 + (threadIdx.x & 31);
-    if (x >= g.V) return;
-    const Coord c = coord_of(g, x);
-    const int64_t xm = x + disp(g, c, mu, 1); // x + mu
+    const int64_t V = g.V;
+    const int xm = x + step32(g, c, mu, 1); // x + mu
+    const auto at = sf.at(sx);
 #pragma unroll 1
     for (int iv = 0; iv < 3; ++iv) {
         const int nu = (mu + 1 + iv) & 3;
-        const int64_t vp = disp(g, c, nu, 1), vm = disp(g, c, nu, -1);
+        const int vp = step32(g, c, nu, 1), vm = step32(g, c, nu, -1);
         // b = +nu:  U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
         // rows 0 and 1 of each staple (which need rows 0 and 1 of the first
         // product only); a full plane takes its third row from them, the
         // staple being a product of three SU(3) links
-        Mat<R> t = mul<N, D>(load_link(links, g.V, nu, xm), load_link(links, g.V, mu, x + vp));
-        Mat<R> up = mul_top2<N, D>(t, load_link(links, g.V, nu, x));
+        Mat<R> t = mul<N, D>(load_link(links, V, nu, xm), load_link(links, V, mu, x + vp));
+        Mat<R> up = mul_top2<N, D>(t, load_link(links, V, nu, x));
         if constexpr (FULL) rebuild_row2(up);
-        Staples<R, FULL>::store(sf, g.V, mu * 6 + 2 * iv, x, up);
+        sf.template store<STREAM>(at, mu * 6 + 2 * iv, up);
         // b = -nu:  U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu)
-        t = mul<D, D>(load_link(links, g.V, nu, xm + vm), load_link(links, g.V, mu, x + vm));
-        Mat<R> dn = mul_top2<N, N>(t, load_link(links, g.V, nu, x + vm));
+        t = mul<D, D>(load_link(links, V, nu, xm + vm), load_link(links, V, mu, x + vm));
+        Mat<R> dn = mul_top2<N, N>(t, load_link(links, V, nu, x + vm));
         if constexpr (FULL) rebuild_row2(dn);
-        Staples<R, FULL>::store(sf, g.V, mu * 6 + 2 * iv + 1, x, dn);
+        sf.template store<STREAM>(at, mu * 6 + 2 * iv + 1, dn);
     }
+}
+
+// The 24 staples of the 32 sites of virtual block vb: thread = (site, mu).
+template <typename R, bool FULL>
+__device__ __forceinline__ void staples_block(const SfLattice &L, const G32 &g, int vb)
+{
+    const int mu = (int)(threadIdx.x >> 5);
+    const int x = vb * 32 + (int)(threadIdx.x & 31);
+    if (x >= g.V) return;
+    site_staples<R, FULL, true>(static_cast<const R *>(L.links), g, coord32(g, x), x, mu,
+                                planes_of<R, FULL>(L), x);
 }
 
 template <typename R, bool FULL>
 __global__ void __launch_bounds__(kBlock) staple_fields(const __grid_constant__ SfLattice L)
 {
-    const Geom g = make_geom(L.dims);
-    const int64_t nvb = virtual_blocks(g.V);
-    for (int64_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) staples_block<R, FULL>(L, g, vb);
+    const G32 g = make_g32(L.dims);
+    const int nvb = (int)virtual_blocks(g.V);
+    for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) staples_block<R, FULL>(L, g, vb);
 }
 
 template <typename R, bool FULL>
@@ -300,7 +419,7 @@ __global__ void __launch_bounds__(kBlock) staple_fields_batched(const __grid_con
          vb = next_virtual_block(B.counter)) {
         const int c = batch_entry(B, vb);
         const SfLattice &L = B.e[c];
-        staples_block<R, FULL>(L, make_geom(L.dims), vb - L.vb_begin);
+        staples_block<R, FULL>(L, make_g32(L.dims), (int)(vb - L.vb_begin));
     }
 }
 
@@ -308,35 +427,49 @@ __global__ void __launch_bounds__(kBlock) staple_fields_batched(const __grid_con
 
 // Products of two SU(3) factors are accumulated as y += s * (a * op(b)) with
 // the third row of the product rebuilt from its first two (mul_acc_su3: the
-// third row of a is never rebuilt), except for full FP64 staples ("direct"),
-// where nothing is rebuilt anyway and plain accumulation with one scaling of
-// the sum measured faster (114 vs 122 ms at 32^3x64: at the 255-register
-// limit the extra temporaries spill).
-template <bool FULL, typename R> constexpr bool direct_products() { return FULL && sizeof(R) == 8; }
-
-template <int FB, bool FULL, typename R>
+// third row of a is never rebuilt or loaded), or (DIRECT, full FP64 staples)
+// as plain products accumulated in full, the sum scaled once: for FP64 that
+// measured faster (114 vs 122 ms at 32^3x64: at the 255-register limit the
+// extra temporaries spill); for FP32 the rebuilt form is faster (3.65 vs
+// 3.75 ms).
+template <int FB, bool DIRECT, typename R>
 __device__ __forceinline__ void acc_su3(Mat<R> &y, const Mat<R> &a, const Mat<R> &b, R s)
 {
-    if constexpr (direct_products<FULL, R>()) mul_acc<N, FB>(y, a, b); // s applied by the caller
+    if constexpr (DIRECT) mul_acc<N, FB>(y, a, b); // s applied by the caller
     else mul_acc_su3<FB>(y, a, b, s);
 }
+
+// Where the staples of a site and of its neighbours are stored.  In the
+// lattice-wide staple field (LatticeSites) that is the site index itself;
+// in the ring of the fused schedule it is a slot of halo'd slices
+// (RingSites, below).
+struct LatticeSites {
+    const G32 *g;
+    const Coord *c;
+    int k;
+    __device__ __forceinline__ int at0() const { return k; }
+    __device__ __forceinline__ int nb(int mu, int s) const { return k + step32(*g, *c, mu, s); }
+};
 
 // The staples that start with link(k+rho, d), d = +-nu_d (NEG: minus):
 //   t += B_d [ c_cube sum_{b perp rho, d} S_b(k+d) S^{(d)}_b(k) + c_rect S_d(k+d) A_d^dag ]
 // (the orientation of the shared links fixed at compile time, so that each
 // sign has one small loop body).
-template <bool NEG, bool UNROLLQ, bool FULL, typename R>
+template <bool NEG, bool UNROLLQ, bool FULL, bool DIRECT, bool COH, typename R, typename SI>
 __device__ __forceinline__ void d_terms(Mat<R> &t, const R *__restrict__ links,
-                                        const R *__restrict__ sf, const Geom &g, const Coord &c,
-                                        int rho, int64_t k, int64_t kp, int id, R c_rt, R c_cb)
+                                        const Planes<R, FULL> &sf, const SI &si, const G32 &g,
+                                        const Coord &c, int rho, int k, int kp, int id, R c_rt,
+                                        R c_cb)
 {
     constexpr int FD = NEG ? D : N;
+    const int64_t V = g.V;
     const int base = rho * 6;
     const int jd = 2 * id + (NEG ? 1 : 0);
     const int nud = (rho + 1 + id) & 3;
-    const int64_t kd = k + disp(g, c, nud, NEG ? -1 : 1); // k + d
+    const int kd = k + step32(g, c, nud, NEG ? -1 : 1); // k + d
     // S^{(d)}_b(k): plane nud*6 + j' at k, or (NEG) its dagger at k - nud = kd
-    const int64_t site2 = NEG ? kd : k;
+    const auto at_d = sf.at(si.nb(nud, NEG ? -1 : 1));
+    const auto at_2 = NEG ? at_d : sf.at(si.at0());
     Mat<R> y;
     set_zero(y);
     // the four signed b perpendicular to rho and d: two directions, two signs
@@ -345,41 +478,36 @@ __device__ __forceinline__ void d_terms(Mat<R> &t, const R *__restrict__ links,
         const int ib = q == 0 ? (id == 0 ? 1 : 0) : (id == 2 ? 1 : 2);
         const int nub = (rho + 1 + ib) & 3;
         const int jp = 2 * ((nub - nud - 1) & 3);
-        using SIO = Staples<R, FULL>;
-        acc_su3<FD, FULL>(y, SIO::load(sf, g.V, base + 2 * ib, kd),
-                          SIO::load(sf, g.V, nud * 6 + jp, site2), c_cb);
-        acc_su3<FD, FULL>(y, SIO::load(sf, g.V, base + 2 * ib + 1, kd),
-                          SIO::load(sf, g.V, nud * 6 + jp + 1, site2), c_cb);
+        acc_su3<FD, DIRECT>(y, sf.template load<COH>(at_d, base + 2 * ib),
+                            sf.template load<COH>(at_2, nud * 6 + jp), c_cb);
+        acc_su3<FD, DIRECT>(y, sf.template load<COH>(at_d, base + 2 * ib + 1),
+                            sf.template load<COH>(at_2, nud * 6 + jp + 1), c_cb);
     }
-    Mat<R> r3 = Staples<R, FULL>::load(sf, g.V, base + jd, kd);
-    if constexpr (direct_products<FULL, R>()) {
+    Mat<R> r3 = sf.template load<COH>(at_d, base + jd);
+    if constexpr (DIRECT) {
         scale(y, c_cb);
         scale(r3, c_rt);
     }
     if constexpr (!NEG) {
-        acc_su3<D, FULL>(y, r3, load_link(links, g.V, nud, k), c_rt); // A_d = U_nud(k)
-        mul_acc<N, N>(t, load_link(links, g.V, nud, kp), y);        // B_d = U_nud(k+rho)
+        acc_su3<D, DIRECT>(y, r3, load_link(links, V, nud, k), c_rt); // A_d = U_nud(k)
+        mul_acc<N, N>(t, load_link(links, V, nud, kp), y);         // B_d = U_nud(k+rho)
     } else {
-        acc_su3<N, FULL>(y, r3, load_link(links, g.V, nud, kd), c_rt); // A_d = U_nud(k-nud)^dag
-        mul_acc<D, N>(t, load_link(links, g.V, nud, kp + (kd - k)), y); // B_d = U_nud(k+rho-nud)^dag
+        acc_su3<N, DIRECT>(y, r3, load_link(links, V, nud, kd), c_rt);  // A_d = U_nud(k-nud)^dag
+        mul_acc<D, N>(t, load_link(links, V, nud, kp + (kd - k)), y);  // B_d = U_nud(k+rho-nud)^dag
     }
 }
 
-// Force (and the fused momentum step) on the 128 links of virtual block vb;
-// returns the thread's share of the action (0 for a padding site).
-template <typename R, bool ACTION, bool UNROLLQ, bool FULL>
-__device__ __forceinline__ double force_block(const SfLattice &L, const KernelScalars &sc,
-                                              const Geom &g, const Sweep &sw, int64_t vb)
+// Force (and the fused momentum step) on the link (k, rho), k at coordinates
+// c, its staples found through si; returns its share of the action.
+template <typename R, bool ACTION, bool UNROLLQ, bool FULL, bool DIRECT, bool COH, typename SI>
+__device__ __forceinline__ double force_link(const SfLattice &L, const KernelScalars &sc, const G32 &g,
+                                             const Planes<R, FULL> &sf, const SI &si, const Coord &c,
+                                             int k, int rho)
 {
     const R *__restrict__ links = static_cast<const R *>(L.links);
-    const R *__restrict__ sf = static_cast<const R *>(L.staples);
-    const int rho = (int)(threadIdx.x >> 5);
-    const int64_t j = vb * 32 + (threadIdx.x & 31);
-    if (j >= g.V) return 0.0;
+    const int64_t V = g.V;
     const R c_pl = scalar<R>(sc, SC_CPL), c_rt = scalar<R>(sc, SC_CRT), c_cb = scalar<R>(sc, SC_CCB);
-    const Coord c = swept_site(sw, j);
-    const int64_t k = index_of(g, c);
-    const int64_t kp = k + disp(g, c, rho, 1), km = k + disp(g, c, rho, -1);
+    const int kp = k + step32(g, c, rho, 1), km = k + step32(g, c, rho, -1);
     const int base = rho * 6;
 
     // plaquettes and the two rectangle chains along rho
@@ -390,48 +518,65 @@ __device__ __forceinline__ double force_block(const SfLattice &L, const KernelSc
         set_zero(pl);
         set_zero(p1);
         set_zero(p2);
+        const auto at_k = sf.at(si.at0()), at_p = sf.at(si.nb(rho, 1)), at_m = sf.at(si.nb(rho, -1));
 #pragma unroll 1
         for (int jj = 0; jj < 6; ++jj) {
-            using SIO = Staples<R, FULL>;
-            const Mat<R> s = SIO::load(sf, g.V, base + jj, k);
+            const Mat<R> s = sf.template load<COH>(at_k, base + jj);
             add_to(pl, s);
-            acc_su3<N, FULL>(p1, SIO::load(sf, g.V, base + jj, kp), s, c_rt);
-            mul_acc<N, N>(p2, s, SIO::load(sf, g.V, base + jj, km));
+            acc_su3<N, DIRECT>(p1, sf.template load<COH>(at_p, base + jj), s, c_rt);
+            mul_acc<N, N>(p2, s, sf.template load<COH>(at_m, base + jj));
         }
-        if constexpr (ACTION) tr_pl = re_trace_mul<N, N>(load_link(links, g.V, rho, k), pl);
+        if constexpr (ACTION) tr_pl = re_trace_mul<N, N>(load_link(links, V, rho, k), pl);
         t = pl;
         scale(t, c_pl);
-        if constexpr (direct_products<FULL, R>()) scale(p1, c_rt);
-        mul_acc<N, N>(t, load_link(links, g.V, rho, kp), p1);
+        if constexpr (DIRECT) scale(p1, c_rt);
+        mul_acc<N, N>(t, load_link(links, V, rho, kp), p1);
         scale(p2, c_rt);
-        mul_acc<N, N>(t, p2, load_link(links, g.V, rho, km));
+        mul_acc<N, N>(t, p2, load_link(links, V, rho, km));
     }
     // cubes and the rectangles along d: positive, then negative d
 #pragma unroll 1
     for (int id = 0; id < 3; ++id)
-        d_terms<false, UNROLLQ, FULL>(t, links, sf, g, c, rho, k, kp, id, c_rt, c_cb);
+        d_terms<false, UNROLLQ, FULL, DIRECT, COH>(t, links, sf, si, g, c, rho, k, kp, id, c_rt, c_cb);
 #pragma unroll 1
     for (int id = 0; id < 3; ++id)
-        d_terms<true, UNROLLQ, FULL>(t, links, sf, g, c, rho, k, kp, id, c_rt, c_cb);
+        d_terms<true, UNROLLQ, FULL, DIRECT, COH>(t, links, sf, si, g, c, rho, k, kp, id, c_rt, c_cb);
 
-    const Mat<R> m = mul<N, N>(load_link(links, g.V, rho, k), t);
+    const Mat<R> m = mul<N, N>(load_link(links, V, rho, k), t);
     R f[8];
     ta_components(m, scalar<R>(sc, SC_BETA6), f);
-    if (L.force != nullptr) store_algebra(static_cast<R *>(L.force), g.V, rho, k, f);
+    if (L.force != nullptr) store_algebra(static_cast<R *>(L.force), V, rho, k, f);
     if (L.mom != nullptr) {
         R *mom = static_cast<R *>(L.mom);
         R p[8];
-        load_algebra(mom, g.V, rho, k, p);
+        load_algebra(mom, V, rho, k, p);
         const R dt = scalar<R>(sc, SC_DT);
 #pragma unroll
         for (int q = 0; q < 8; ++q) p[q] = fma(dt, f[q], p[q]);
-        store_algebra(mom, g.V, rho, k, p);
+        store_algebra(mom, V, rho, k, p);
     }
     if constexpr (ACTION) {
         const R tr_t = m.re[0][0] + m.re[1][1] + m.re[2][2];
         return (double)(scalar<R>(sc, SC_ACT) - tr_t * R(1.0 / 6.0) - scalar<R>(sc, SC_ACTPL) * tr_pl);
     }
     return 0.0;
+}
+
+// Force (and the fused momentum step) on the 128 links of virtual block vb
+// of the sweep; returns the thread's share of the action (0 for a padding
+// site).
+template <typename R, bool ACTION, bool UNROLLQ, bool FULL, bool DIRECT>
+__device__ __forceinline__ double force_block(const SfLattice &L, const KernelScalars &sc,
+                                              const G32 &g, const Sweep &sw, int vb)
+{
+    const int rho = (int)(threadIdx.x >> 5);
+    const int j = vb * 32 + (int)(threadIdx.x & 31);
+    if (j >= g.V) return 0.0;
+    const Coord c = swept_site(sw, j);
+    const int k = index32(g, c);
+    const LatticeSites si{&g, &c, k};
+    return force_link<R, ACTION, UNROLLQ, FULL, DIRECT, false>(L, sc, g, planes_of<R, FULL>(L), si, c,
+                                                               k, rho);
 }
 
 // Resident CTAs per SM the register allocation aims at: 4 (128 registers)
@@ -441,15 +586,19 @@ template <typename R, bool ACTION, bool DENSE> constexpr int min_blocks()
     return sizeof(R) == 8 ? 2 : ((ACTION && !DENSE) ? 3 : 4);
 }
 
-template <typename R, bool ACTION, bool UNROLLQ, bool DENSE = false, bool FULL = false>
+// DIRECT products by default for full FP64 planes (see acc_su3).
+template <typename R, bool FULL> constexpr bool direct_default() { return FULL && sizeof(R) == 8; }
+
+template <typename R, bool ACTION, bool UNROLLQ, bool DENSE = false, bool FULL = false,
+          bool DIRECT = direct_default<R, FULL>()>
 __global__ void __launch_bounds__(kBlock, (min_blocks<R, ACTION, DENSE>()))
     force_from_staples(const __grid_constant__ SfLattice L, const __grid_constant__ KernelScalars sc)
 {
-    const Geom g = make_geom(L.dims);
+    const G32 g = make_g32(L.dims);
     const Sweep sw = make_sweep(L, g);
-    const int64_t nvb = virtual_blocks(g.V);
-    for (int64_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
-        const double acc = force_block<R, ACTION, UNROLLQ, FULL>(L, sc, g, sw, vb);
+    const int nvb = (int)virtual_blocks(g.V);
+    for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+        const double acc = force_block<R, ACTION, UNROLLQ, FULL, DIRECT>(L, sc, g, sw, vb);
         if constexpr (ACTION) {
             const double s = block_sum(acc);
             if (threadIdx.x == 0) L.partials[vb] = s;
@@ -457,7 +606,8 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<R, ACTION, DENSE>()))
     }
 }
 
-template <typename R, bool ACTION, bool UNROLLQ, bool DENSE = false, bool FULL = false>
+template <typename R, bool ACTION, bool UNROLLQ, bool DENSE = false, bool FULL = false,
+          bool DIRECT = direct_default<R, FULL>()>
 __global__ void __launch_bounds__(kBlock, (min_blocks<R, ACTION, DENSE>()))
     force_from_staples_batched(const __grid_constant__ SfBatch B,
                                const __grid_constant__ KernelScalars sc)
@@ -466,13 +616,233 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<R, ACTION, DENSE>()))
          vb = next_virtual_block(B.counter + 1)) {
         const int c = batch_entry(B, vb);
         const SfLattice &L = B.e[c];
-        const Geom g = make_geom(L.dims);
-        const double acc =
-            force_block<R, ACTION, UNROLLQ, FULL>(L, sc, g, make_sweep(L, g), vb - L.vb_begin);
+        const G32 g = make_g32(L.dims);
+        const double acc = force_block<R, ACTION, UNROLLQ, FULL, DIRECT>(
+            L, sc, g, make_sweep(L, g), (int)(vb - L.vb_begin));
         if constexpr (ACTION) {
             const double s = block_sum(acc);
             if (threadIdx.x == 0) L.partials[vb - L.vb_begin] = s;
         }
+    }
+}
+
+// ------------------------------------------------------------ fused schedule
+//
+// The staples of the lattice never go to HBM: the lattice is cut into
+// spatial blocks of whole x rows (by x bz rows), and each block is swept
+// along t.  "A" items compute the staples of one t-slice of a block and of
+// its y/z halo of one row into a ring of R slots that stays in L2; "B"
+// items compute the force on one slice of the block from the three slices
+// t-1, t, t+1 of the ring.  Items are handed out in a fixed order from a
+// work counter (per block: A(t=-1), A(0), then A(t+1), B(t) for t = 0 ..
+// L3-1; the slices -1 and L3 are the periodic images L3-1 and 0, computed
+// again into their own slots), and an item waits only for items handed out
+// before it: a B item for the three A slices it reads, an A item for the B
+// items that read the slot's previous slice.  Every resident block works
+// on the lowest unfinished items, so the waits always end; each is bounded
+// anyway (after about two seconds the item sets an error word, the action
+// comes out NaN, and the launch still ends).  The halo rows are computed
+// twice (by the neighbouring blocks too): 1 + 2/by + 2/bz + 4/(by bz) times
+// the staple work, in exchange for staples that are written to and read
+// from L2 only.
+
+// The fused schedule's geometry and buffers (filled on the host).
+struct Ring {
+    int by, bz;          // rows of a spatial block along y, z (blocks hold whole x rows)
+    int nby, nbz;        // blocks along y, z
+    int ry;              // halo'd rows along y (by + 2)
+    int nring;           // sites of one slot: L0 (by + 2) (bz + 2)
+    int R;               // slots
+    int nA, nB;          // virtual blocks of an A slice and of a B slice
+    int per_block;       // items of one block: 2 nA + L3 (nA + nB)
+    int nslices;         // slices of all blocks: blocks (L3 + 2)
+    int64_t total;       // items of the launch
+    int *a_done;         // per slice: A items finished
+    int *b_done;         // per slice, as the centre of B items: B items finished
+    unsigned long long *work; // item counter
+    unsigned int *error; // set when a wait ran out
+    char *ring;          // staple planes of the R slots (full form)
+    int64_t plane_bytes;
+};
+
+struct RingSites {
+    const Ring *r;
+    int L0, x, yr, zr, slot;
+    __device__ __forceinline__ int idx(int x_, int yr_, int zr_, int slot_) const
+    {
+        return slot_ * r->nring + (zr_ * r->ry + yr_) * L0 + x_;
+    }
+    __device__ __forceinline__ int at0() const { return idx(x, yr, zr, slot); }
+    __device__ __forceinline__ int nb(int mu, int s) const
+    {
+        if (mu == 0) {
+            const int x2 = x + s;
+            return idx(x2 < 0 ? L0 - 1 : (x2 == L0 ? 0 : x2), yr, zr, slot);
+        }
+        if (mu == 1) return idx(x, yr + s, zr, slot);
+        if (mu == 2) return idx(x, yr, zr + s, slot);
+        const int s2 = slot + s;
+        return idx(x, yr, zr, s2 < 0 ? r->R - 1 : (s2 == r->R ? 0 : s2));
+    }
+};
+
+constexpr int kWaitPolls = 1 << 25;             // hard bound on the polls of one wait
+constexpr unsigned long long kWaitNs = 2000000000ull; // and on its duration
+
+// Polls use relaxed loads: an acquire also discards the SM's L1 contents,
+// which the other blocks on the SM are using; one acquire fence follows
+// once the counts are reached.
+__device__ __forceinline__ int load_relaxed(const int *p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Thread 0 waits until *ctr >= target (bounded; on a timeout the error word
+// is set and the item goes on; once the word is set no wait of the launch
+// waits any more, so a launch that went wrong still ends promptly).
+__device__ __forceinline__ void wait_count(const int *ctr, int target, unsigned int *error)
+{
+    if (load_relaxed(ctr) < target) {
+        const volatile unsigned int *err = error;
+        const unsigned long long t0 = global_ns();
+        int i = 0;
+        for (; i < kWaitPolls; ++i) {
+            if (*err != 0u) return;
+            __nanosleep(128);
+            if (load_relaxed(ctr) >= target) break;
+            if ((i & 255) == 255 && global_ns() - t0 > kWaitNs) {
+                i = kWaitPolls;
+                break;
+            }
+        }
+        if (i == kWaitPolls) atomicOr(error, 1u);
+    }
+}
+
+// After the relaxed polls of an item's waits: the acquire that orders the
+// block's following reads after the producers' writes (one per item).
+__device__ __forceinline__ void acquire_fence()
+{
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
+// Is global slice c the centre of a B slice (and not a block's halo slice)?
+__device__ __forceinline__ bool b_centre(const Ring &F, int L3, int c)
+{
+    if (c < 0 || c >= F.nslices) return false;
+    const int s = c % (L3 + 2);
+    return s >= 1 && s <= L3;
+}
+
+template <typename R, bool ACTION>
+__global__ void __launch_bounds__(kBlock, (min_blocks<R, ACTION, true>()))
+    force_fused(const __grid_constant__ SfLattice L, const __grid_constant__ KernelScalars sc,
+                const __grid_constant__ Ring F)
+{
+    const G32 g = make_g32(L.dims);
+    const Planes<R, true> ring{F.ring, F.plane_bytes};
+    const int w = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
+    for (int64_t it = next_virtual_block(F.work); it < F.total; it = next_virtual_block(F.work)) {
+        const int b = (int)(it / F.per_block);
+        int i = (int)(it - (int64_t)b * F.per_block);
+        bool is_a;
+        int sl, vb; // local slice (t + 1) and virtual block within the slice
+        if (i < 2 * F.nA) {
+            is_a = true;
+            sl = i / F.nA;
+            vb = i - sl * F.nA;
+        } else {
+            i -= 2 * F.nA;
+            const int pair = i / (F.nA + F.nB), r = i - pair * (F.nA + F.nB);
+            is_a = r < F.nA;
+            sl = is_a ? pair + 2 : pair + 1;
+            vb = is_a ? r : r - F.nA;
+        }
+        const int gs = b * (g.L3 + 2) + sl;
+        const int slot = gs % F.R;
+        const int by0 = (b % F.nby) * F.by, bz0 = (b / F.nby) * F.bz;
+        if (is_a) {
+            // the slot's previous slice must have been read by all its B items
+            if (threadIdx.x == 0) {
+                for (int c = gs - F.R - 1; c <= gs - F.R + 1; ++c)
+                    if (b_centre(F, g.L3, c)) wait_count(F.b_done + c, F.nB, F.error);
+                acquire_fence();
+            }
+            __syncthreads();
+            const int rr = vb * 32 + lane;
+            if (rr < F.nring) {
+                Coord c;
+                c.c0 = rr % g.L0;
+                const int q = rr / g.L0, yr = q % F.ry, zr = q / F.ry;
+                c.c1 = ((by0 + yr - 1) % g.L1 + g.L1) % g.L1;
+                c.c2 = ((bz0 + zr - 1) % g.L2 + g.L2) % g.L2;
+                c.c3 = ((sl - 1) % g.L3 + g.L3) % g.L3;
+                site_staples<R, true, false>(static_cast<const R *>(L.links), g, c, index32(g, c), w,
+                                             ring, slot * F.nring + rr);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(F.a_done + gs, 1);
+            }
+        } else {
+            if (threadIdx.x == 0) {
+                for (int c = gs - 1; c <= gs + 1; ++c) wait_count(F.a_done + c, F.nA, F.error);
+                acquire_fence();
+            }
+            __syncthreads();
+            const int t = sl - 1;
+            const int ii = vb * 32 + lane;
+            double acc = 0.0;
+            if (ii < g.L0 * F.by * F.bz) {
+                const int x = ii % g.L0, q = ii / g.L0, y = q % F.by, z = q / F.by;
+                const Coord c{x, by0 + y, bz0 + z, t};
+                const int k = index32(g, c);
+                const RingSites si{&F, g.L0, x, y + 1, z + 1, slot};
+                acc = force_link<R, ACTION, false, true, direct_default<R, true>(), true>(
+                    L, sc, g, ring, si, c, k, w);
+            }
+            if constexpr (ACTION) {
+                const double s = block_sum(acc);
+                if (threadIdx.x == 0) L.partials[((int64_t)b * g.L3 + t) * F.nB + vb] = s;
+            } else {
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) {
+                __threadfence(); // the block's reads of the ring come before the release
+                atomicAdd(F.b_done + gs, 1);
+            }
+        }
+    }
+}
+
+// The action from the fused schedule's partial sums (fixed order), NaN if a
+// wait of the launch ran out.
+__global__ void __launch_bounds__(1024) finish_fused(const double *partials, int count, double scale,
+                                                     const unsigned int *error, double *out)
+{
+    __shared__ double warp_part[32];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < count; i += 1024) v += partials[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) warp_part[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double s = warp_part[lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) *out = *error != 0u ? __longlong_as_double(0x7ff8000000000000ll) : scale * s;
     }
 }
 
@@ -482,7 +852,7 @@ __global__ void __launch_bounds__(1024) finish_batched(const __grid_constant__ S
 {
     const SfLattice &L = B.e[blockIdx.x];
     if (L.action == nullptr) return;
-    const int count = (int)virtual_blocks(make_geom(L.dims).V);
+    const int count = (int)virtual_blocks((int64_t)L.dims[0] * L.dims[1] * L.dims[2] * L.dims[3]);
     __shared__ double warp_part[32];
     double v = 0.0;
     for (int i = threadIdx.x; i < count; i += 1024) v += L.partials[i];
@@ -517,22 +887,25 @@ unsigned grid_of(int64_t items)
 //      4.45 ms with 64x16x16 at 32^3x64 FP32)
 //   5  as 4, registers capped for 4 CTAs/SM
 //   6  as 4 with spatial blocks up to 64x16x16
+//   7  fused: no lattice-wide staple field; the staples of each t-slice of a
+//      spatial block (with a halo row) are computed into an L2-resident
+//      ring just ahead of the force items that read them (one launch)
 // The process-wide choice per precision is set by lqcd_set_force_variant or
-// lqcd_autotune_force; -1 means the default: x rows with full staples in both
-// precisions (at 32^3x64: FP32 4.64 vs 4.75 ms with compact staples, FP64
-// 114 vs 128 ms).
-constexpr int kSfVariants = 7;
+// lqcd_autotune_force; -1 means the default: x rows with full staples, in
+// FP32 with the 4-CTA register cap (at 32^3x64: FP32 3.62 ms, 3.65 uncapped,
+// 4.28 with compact staples; FP64 110 vs 128 ms).
+constexpr int kSfVariants = 8;
 
 bool full_staples(int variant) { return variant >= 4; }
 
 // Slot of a kernel instance in the occupancy cache of persistent_grid:
 // kind (0 pass B, 1 pass B capped, 2 pass B full, 3 pass B full capped,
-// 4 pass A compact, 5 pass A full) x precision x action x unrolled.
+// 4 pass A compact, 5 pass A full, 6 fused) x precision x action x unrolled.
 int grid_slot(int kind, bool f64, bool action, bool unrolled)
 {
     return kind * 8 + (f64 ? 4 : 0) + (action ? 2 : 0) + (unrolled ? 1 : 0);
 }
-constexpr int kSfDefault[2] = {4, 4};
+constexpr int kSfDefault[2] = {5, 4};
 std::atomic<int> g_sf_variant[2] = {{-1}, {-1}};
 
 // Largest divisor of L not above cap.
@@ -545,7 +918,7 @@ int block_extent(int L, int cap)
 
 void set_traversal(SfLattice &L, int variant)
 {
-    const int cap_yz = (variant == 4 || variant == 5) ? 8 : 16;
+    const int cap_yz = (variant == 4 || variant == 5 || variant == 7) ? 8 : 16;
     L.sweep[0] = block_extent(L.dims[0], 64);
     L.sweep[1] = block_extent(L.dims[1], cap_yz);
     L.sweep[2] = block_extent(L.dims[2], cap_yz);
@@ -610,6 +983,7 @@ cudaError_t launch_pass_b(const SfLattice &L, const KernelScalars &sc, int varia
     else if (variant == 3) force_from_staples<R, ACTION, false, true><<<grid, kBlock, 0, st>>>(L, sc);
     else if (variant == 4 || variant == 6)
         force_from_staples<R, ACTION, false, false, true><<<grid, kBlock, 0, st>>>(L, sc);
+
     else if (variant == 5)
         force_from_staples<R, ACTION, false, true, true><<<grid, kBlock, 0, st>>>(L, sc);
     else force_from_staples<R, ACTION, false><<<grid, kBlock, 0, st>>>(L, sc);
@@ -630,9 +1004,10 @@ cudaError_t launch_pass_b_batched(const SfBatch &B, const KernelScalars &sc, int
     } else if (variant == 4 || variant == 6) {
         auto k = force_from_staples_batched<R, ACTION, false, false, true>;
         k<<<persistent_grid(k, grid_slot(2, f64, ACTION, false), B.total), kBlock, 0, st>>>(B, sc);
-    } else if (variant == 5) {
+    } else if (variant == 5 || variant == 7) { // the fused schedule is single-lattice only
         auto k = force_from_staples_batched<R, ACTION, false, true, true>;
         k<<<persistent_grid(k, grid_slot(3, f64, ACTION, false), B.total), kBlock, 0, st>>>(B, sc);
+
     } else {
         auto k = force_from_staples_batched<R, ACTION, false>;
         k<<<persistent_grid(k, grid_slot(0, f64, ACTION, false), B.total), kBlock, 0, st>>>(B, sc);
@@ -640,12 +1015,101 @@ cudaError_t launch_pass_b_batched(const SfBatch &B, const KernelScalars &sc, int
     return cudaGetLastError();
 }
 
+// Geometry of the fused schedule: spatial blocks of up to 8 x 8 rows, fewer
+// where one slot would pass 6 MB (six slots then take at most 36 MB of L2).
+Ring ring_shape(const int dims[4], int precision)
+{
+    const size_t site_bytes = (size_t)kStaplePlanes * 18 * (precision == LQCD_F64 ? 8 : 4);
+    const size_t cap = (size_t)6 << 20;
+    int by = block_extent(dims[1], 8), bz = block_extent(dims[2], 8);
+    while ((size_t)dims[0] * (by + 2) * (bz + 2) * site_bytes > cap && (by > 1 || bz > 1)) {
+        if (by >= bz) by = block_extent(dims[1], by - 1);
+        else bz = block_extent(dims[2], bz - 1);
+    }
+    Ring F{};
+    F.by = by;
+    F.bz = bz;
+    F.nby = dims[1] / by;
+    F.nbz = dims[2] / bz;
+    F.ry = by + 2;
+    F.nring = dims[0] * (by + 2) * (bz + 2);
+    F.R = 6;
+    F.nA = (F.nring + 31) / 32;
+    F.nB = (dims[0] * by * bz + 31) / 32;
+    F.per_block = 2 * F.nA + dims[3] * (F.nA + F.nB);
+    F.nslices = F.nby * F.nbz * (dims[3] + 2);
+    F.total = (int64_t)F.nby * F.nbz * F.per_block;
+    return F;
+}
+
+size_t round_up256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Workspace of the fused schedule, from its start: the ring's planes, the
+// two counter arrays, the item counter and the error word.
+size_t fused_ring_bytes(const Ring &F, int precision)
+{
+    return round_up256((size_t)kStaplePlanes * full_plane_bytes((int64_t)F.R * F.nring, precision));
+}
+
+size_t fused_bytes(const int dims[4], int precision)
+{
+    const Ring F = ring_shape(dims, precision);
+    return fused_ring_bytes(F, precision) + round_up256(2 * (size_t)F.nslices * sizeof(int)) + 256;
+}
+
+int fused_partials(const int dims[4])
+{
+    const Ring F = ring_shape(dims, LQCD_F32); // the block shape does not change the count much
+    const Ring G = ring_shape(dims, LQCD_F64);
+    const int64_t a = (int64_t)F.nby * F.nbz * dims[3] * F.nB, b = (int64_t)G.nby * G.nbz * dims[3] * G.nB;
+    return (int)(a > b ? a : b);
+}
+
+template <typename R> cudaError_t launch_fused_t(const ForceArgs &a, const KernelScalars &sc, cudaStream_t st)
+{
+    SfLattice L{};
+    for (int i = 0; i < 4; ++i) L.dims[i] = a.dims[i];
+    L.links = a.links;
+    L.force = a.force;
+    L.mom = a.mom;
+    L.partials = a.partials;
+    L.action = a.action;
+    Ring F = ring_shape(a.dims, a.precision);
+    char *ws = static_cast<char *>(a.staples);
+    F.ring = ws;
+    F.plane_bytes = (int64_t)full_plane_bytes((int64_t)F.R * F.nring, a.precision);
+    char *ctr = ws + fused_ring_bytes(F, a.precision);
+    F.a_done = reinterpret_cast<int *>(ctr);
+    F.b_done = F.a_done + F.nslices;
+    char *tail = ctr + round_up256(2 * (size_t)F.nslices * sizeof(int));
+    F.work = reinterpret_cast<unsigned long long *>(tail);
+    F.error = reinterpret_cast<unsigned int *>(tail + 8);
+    cudaError_t e = cudaMemsetAsync(ctr, 0, (size_t)(tail + 16 - ctr), st);
+    if (e != cudaSuccess) return e;
+    constexpr bool f64 = sizeof(R) == 8;
+    if (a.action != nullptr) {
+        auto k = force_fused<R, true>;
+        k<<<persistent_grid(k, grid_slot(6, f64, true, false), F.total), kBlock, 0, st>>>(L, sc, F);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const int count = (int)((int64_t)F.nby * F.nbz * a.dims[3] * F.nB);
+        finish_fused<<<1, 1024, 0, st>>>(a.partials, count, a.beta / 3.0, F.error, a.action);
+    } else {
+        auto k = force_fused<R, false>;
+        k<<<persistent_grid(k, grid_slot(6, f64, false, false), F.total), kBlock, 0, st>>>(L, sc, F);
+    }
+    return cudaGetLastError();
+}
+
 template <typename R> cudaError_t launch_sf_t(const ForceArgs &a, cudaStream_t st)
 {
     const int variant = resolve_variant(a);
+    if (variant == 7) return launch_fused_t<R>(a, make_scalars(a), st);
     SfLattice L{};
     for (int i = 0; i < 4; ++i) L.dims[i] = a.dims[i];
     set_traversal(L, variant);
+    L.plane_bytes = (int64_t)full_plane_bytes((int64_t)a.dims[0] * a.dims[1] * a.dims[2] * a.dims[3],
+                                              a.precision);
     L.links = a.links;
     L.staples = a.staples;
     L.force = a.force;
@@ -679,6 +1143,9 @@ cudaError_t launch_sf_batched_t(const ForceArgs &a, int n, const SfLattice *item
     for (int c = 0; c < n; ++c) {
         B.e[c] = items[c];
         set_traversal(B.e[c], variant);
+        B.e[c].plane_bytes = (int64_t)full_plane_bytes(
+            (int64_t)items[c].dims[0] * items[c].dims[1] * items[c].dims[2] * items[c].dims[3],
+            a.precision);
         B.e[c].vb_begin = vb;
         vb += virtual_blocks((int64_t)items[c].dims[0] * items[c].dims[1] * items[c].dims[2] *
                              items[c].dims[3]);
@@ -706,18 +1173,27 @@ cudaError_t launch_sf_batched_t(const ForceArgs &a, int n, const SfLattice *item
 
 } // namespace
 
-// Room for the 24 planes in the larger (full, 18-real) of the two storage
-// forms, so that every schedule fits the same workspace.
+// Room for the 24 planes in the larger (full, 18-real, in blocks of 32
+// sites) of the two storage forms, so that every schedule fits the same
+// workspace.
 size_t staple_field_bytes(const int dims[4], int precision)
 {
     const int64_t V = (int64_t)dims[0] * dims[1] * dims[2] * dims[3];
-    const size_t real = precision == LQCD_F64 ? 8 : 4;
-    return ((size_t)kStaplePlanes * 18 * real * (size_t)V + 255) & ~(size_t)255;
+    const size_t two_pass = round_up256((size_t)kStaplePlanes * full_plane_bytes(V, precision));
+    const size_t fused = fused_bytes(dims, precision);
+    return two_pass > fused ? two_pass : fused;
+}
+
+bool staple_fields_supported(const int dims[4])
+{
+    return (int64_t)dims[0] * dims[1] * dims[2] * dims[3] < ((int64_t)1 << 31);
 }
 
 int staple_force_partials(const int dims[4])
 {
-    return (int)virtual_blocks((int64_t)dims[0] * dims[1] * dims[2] * dims[3]);
+    const int a = (int)virtual_blocks((int64_t)dims[0] * dims[1] * dims[2] * dims[3]);
+    const int b = fused_partials(dims);
+    return a > b ? a : b;
 }
 
 cudaError_t launch_force_staple_fields(const ForceArgs &a, cudaStream_t st)

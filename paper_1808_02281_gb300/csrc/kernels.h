@@ -66,6 +66,7 @@ struct SfLattice {
     int sweep[3];      // spatial block extents of the pass-B traversal
     int micro[3];      // micro-tile extents inside a block slice
     int64_t vb_begin;  // batch: first virtual block of this lattice
+    int64_t plane_bytes; // full staple planes: bytes of one plane
     const void *links;
     void *staples;     // 24 staple planes (workspace)
     void *force;       // written when set
@@ -92,6 +93,8 @@ cudaError_t launch_force(const ForceArgs &a, cudaStream_t st);
 // Staple-field algorithm (force_sf.cu): workspace bytes of the 24 staple
 // planes, number of per-block action partials, and the two-pass launch.
 size_t staple_field_bytes(const int dims[4], int precision);
+// The staple-field kernels index sites with 32-bit integers: V < 2^31.
+bool staple_fields_supported(const int dims[4]);
 int staple_force_partials(const int dims[4]);
 cudaError_t launch_force_staple_fields(const ForceArgs &a, cudaStream_t st);
 // a: precision, coefficients, dt, variant; items: the lattices (their dims,

@@ -446,39 +446,70 @@ template <typename R> __device__ __forceinline__ Mat<R> exp_i_hermitian(Mat<R> q
     return e;
 }
 
+// Row i scaled to unit length: u <- u + u c with c = 1/|u| - 1 written as
+// -d / (r (1 + r)), d = |u|^2 - 1, r = |u|.  The plain form u <- u * (1/|u|)
+// rounds the factor 1/|u| to a grid point next to 1, where the spacing is
+// 2^-24 below 1 and 2^-23 above it, so that for rows that are already nearly
+// normalised (every link step) FP32 rows came out longer on average
+// (|u|^2 - 1 = +5e-8 over random SU(3) matrices: an action offset of about
+// 1e-7 relative, 5 at 48^3x96).  Here the small correction c keeps its full
+// relative precision and each entry is rounded once (FMA); in FP32 d is also
+// formed without rounding bias: every square is split exactly into its
+// rounded value and error by an FMA, the rounded values are added with
+// their errors kept (two-sum), and 1 is subtracted from the leading part
+// (exact for a sum within a factor 2 of 1).  The mean of |u|^2 - 1 is then
+// below 1e-10 in FP32 (it was -1e-8 with d from a plain FP32 sum).
+template <typename R> __device__ __forceinline__ void normalise_row(Mat<R> &u, int i)
+{
+    R d;
+    if constexpr (sizeof(R) == 4) {
+        R s = R(0), e = R(0);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            const R x = (j & 1) ? u.im[i][j >> 1] : u.re[i][j >> 1];
+            const R p = __fmul_rn(x, x); // never contracted into an FMA
+            const R pe = fma(x, x, -p);
+            const R t = s + p;
+            const R bb = t - s;
+            e += ((s - (t - bb)) + (p - bb)) + pe;
+            s = t;
+        }
+        d = (s - R(1)) + e;
+    } else {
+        R s = R(0);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            s = fma(u.re[i][j], u.re[i][j], s);
+            s = fma(u.im[i][j], u.im[i][j], s);
+        }
+        d = s - R(1);
+    }
+    const R r = sqrt(R(1) + d);
+    const R c = -d / (r * (R(1) + r));
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        u.re[i][j] = fma(u.re[i][j], c, u.re[i][j]);
+        u.im[i][j] = fma(u.im[i][j], c, u.im[i][j]);
+    }
+}
+
 // Gram-Schmidt of rows 0 and 1, then row 2 = conj(row0 x row1).
 template <typename R> __device__ __forceinline__ void reunitarise(Mat<R> &u)
 {
-    R n0 = R(0);
-#pragma unroll
-    for (int j = 0; j < 3; ++j) n0 += u.re[0][j] * u.re[0][j] + u.im[0][j] * u.im[0][j];
-    n0 = R(1) / sqrt(n0);
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        u.re[0][j] *= n0;
-        u.im[0][j] *= n0;
-    }
+    normalise_row(u, 0);
     // proj = <row0, row1> = sum conj(u0j) u1j
     R pr = R(0), pi = R(0);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        pr += u.re[0][j] * u.re[1][j] + u.im[0][j] * u.im[1][j];
-        pi += u.re[0][j] * u.im[1][j] - u.im[0][j] * u.re[1][j];
+        pr = fma(u.re[0][j], u.re[1][j], fma(u.im[0][j], u.im[1][j], pr));
+        pi = fma(u.re[0][j], u.im[1][j], fma(-u.im[0][j], u.re[1][j], pi));
     }
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        u.re[1][j] -= pr * u.re[0][j] - pi * u.im[0][j];
-        u.im[1][j] -= pr * u.im[0][j] + pi * u.re[0][j];
+        u.re[1][j] = fma(-pr, u.re[0][j], fma(pi, u.im[0][j], u.re[1][j]));
+        u.im[1][j] = fma(-pr, u.im[0][j], fma(-pi, u.re[0][j], u.im[1][j]));
     }
-    R n1 = R(0);
-#pragma unroll
-    for (int j = 0; j < 3; ++j) n1 += u.re[1][j] * u.re[1][j] + u.im[1][j] * u.im[1][j];
-    n1 = R(1) / sqrt(n1);
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        u.re[1][j] *= n1;
-        u.im[1][j] *= n1;
-    }
+    normalise_row(u, 1);
     rebuild_row2(u);
 }
 

@@ -23,7 +23,10 @@ plaquette, the FP64 unitarity deviation of the links); ``save_checkpoint`` / ``l
 state so that a resumed run continues bit for bit.
 
 ``python -m paper_1808_02281_gb300.hmc`` runs the dH-versus-dt study;
-``--hmc N`` runs N HMC trajectories instead (JSON line per trajectory).
+``--same-start`` runs it from one thermalised start shared by the FP32 and
+FP64 trajectories (same values), so that their dH difference is the error of
+the FP32 arithmetic alone; ``--hmc N`` runs N HMC trajectories instead (JSON
+line per trajectory).
 """
 from __future__ import annotations
 
@@ -247,6 +250,86 @@ def dh_study(dims, tau: float, dts, integrator: str, precisions, seed: int = 0):
             torch.cuda.empty_cache()
 
 
+def thermalise(st: MDState, n: int, tau: float, dt: float, integrator: str = "omelyan",
+               seed: int = 0):
+    """n molecular-dynamics trajectories with a momentum refresh before each
+    and no accept/reject step: moves a synthetic start towards the typical
+    configurations of the action, where the force is that of an equilibrium
+    ensemble rather than of random links.  Momenta of trajectory t come from
+    the counter-based stream word t of ``seed``.  Yields the trajectory's
+    dH (in the state's own precision), then S and the plaquette after it."""
+    nsteps = max(1, int(round(tau / dt)))
+    for t in range(n):
+        lqcd.gaussian_momenta(st.lat, _stream_word(seed, t), out=st.mom)
+        H0 = hamiltonian(st)
+        INTEGRATORS[integrator](st, tau / nsteps, nsteps)
+        H1 = hamiltonian(st)
+        S = float(lqcd.gauge_action(st.lat, st.links, workspace=st.workspace).item())
+        yield {"trajectory": t, "dH": H1 - H0, "action": S, "plaquette": plaquette(st)}
+
+
+def same_start_pair(links32: torch.Tensor, lat32: lqcd.Lattice, momentum_stream: int):
+    """An FP32 state and an FP64 state that hold the same values: the FP32
+    links and GPU-drawn FP32 momenta, and both promoted exactly to FP64."""
+    mom32 = lqcd.gaussian_momenta(lat32, momentum_stream, device=links32.device)
+    a = MDState.create(lat32, links32.clone(), mom32)
+    lat64 = lat32.with_(precision="f64")
+    b = MDState.create(lat64, lqcd.convert_links(lat32, links32, "f64"),
+                       lqcd.convert_algebra(lat32, mom32, "f64"))
+    return a, b
+
+
+def same_start_study(dims, tau: float, dts, integrator: str = "omelyan", seed: int = 0,
+                     n_therm: int = 100, therm_tau: float = 0.5, therm_dt: float = 0.025,
+                     sigma: float = 0.3, u0: float = 0.87, beta: float = 6.0):
+    """dH of FP32 and FP64 trajectories that start from the same state.
+
+    The synthetic start (links exp(i w.T), w ~ N(0, sigma^2)) is first
+    thermalised in FP32 (n_therm trajectories, see thermalise()) and
+    reunitarised in FP64 (rounded to FP32); then for
+    every dt one FP32 trajectory runs on the thermalised links with FP32
+    momenta drawn on the GPU, and one FP64 trajectory on the same values
+    promoted exactly.  H = K + S in FP64 in both (the FP32 run's action in
+    FP64 arithmetic of its stored links), so H0 is the same number in both
+    runs and dH_f32 - dH_f64 is the error of the FP32 arithmetic alone.
+    Yields the thermalisation records, then one record per dt."""
+    st = initial_state(dims, "f32", sigma, u0, beta, seed)
+    for rec in thermalise(st, n_therm, therm_tau, therm_dt, integrator, seed + 101):
+        rec["phase"] = "thermalise"
+        yield rec
+    # start from links that are in SU(3) to FP64 accuracy before rounding
+    # (Gram-Schmidt in FP64, rounded to FP32), so that neither run starts
+    # with a systematic departure that only the FP64 run would remove
+    lqcd.reunitarise_links(st.lat, st.links)
+    links32 = st.links.clone()
+    lat32 = st.lat
+    del st
+    torch.cuda.empty_cache()
+    for dt in dts:
+        # the same momenta for every dt, so that dH(dt) follows one trajectory
+        a, b = same_start_pair(links32, lat32, _stream_word(seed + 202, 0))
+        nsteps = max(1, int(round(tau / dt)))
+        rec = {"phase": "study", "dims": list(dims), "tau": tau, "dt": tau / nsteps, "nsteps": nsteps,
+               "integrator": integrator, "forces": force_evaluations(integrator, nsteps)}
+        H0a, H0b = hamiltonian(a, "f64"), hamiltonian(b)
+        H0a_own = hamiltonian(a)
+        rec["H0"] = H0b
+        rec["H0_equal"] = H0a == H0b
+        for name, stt in (("f32", a), ("f64", b)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            INTEGRATORS[integrator](stt, tau / nsteps, nsteps)
+            torch.cuda.synchronize()
+            rec[f"seconds_{name}"] = time.perf_counter() - t0
+        rec["dH_f32"] = hamiltonian(a, "f64") - H0a
+        rec["dH_f32_f32action"] = hamiltonian(a) - H0a_own
+        rec["dH_f64"] = hamiltonian(b) - H0b
+        rec["abs_diff"] = abs(rec["dH_f32"] - rec["dH_f64"])
+        yield rec
+        del a, b
+        torch.cuda.empty_cache()
+
+
 # ------------------------------------------------------------- HMC runs
 
 def plaquette(st: MDState) -> float:
@@ -456,6 +539,11 @@ def main(argv=None):
     ap.add_argument("--hmc", type=int, default=0, metavar="N",
                     help="run N HMC trajectories (first precision, first dt) instead of the study")
     ap.add_argument("--checkpoint", default=None, help="HMC: checkpoint file (resumed if present)")
+    ap.add_argument("--same-start", action="store_true",
+                    help="FP32 and FP64 trajectories from one thermalised start (same values)")
+    ap.add_argument("--therm", type=int, default=100, help="same-start: thermalising trajectories")
+    ap.add_argument("--therm-tau", type=float, default=0.5)
+    ap.add_argument("--therm-dt", type=float, default=0.025)
     args = ap.parse_args(argv)
     from . import build
     build.build()
@@ -470,6 +558,11 @@ def main(argv=None):
         else:
             st = initial_state(tuple(args.dims), prec, seed=args.seed)
         for rec in run_hmc(st, cfg, args.hmc, start=start, checkpoint=args.checkpoint, every=1):
+            print(json.dumps(rec), flush=True)
+        return
+    if args.same_start:
+        for rec in same_start_study(tuple(args.dims), args.tau, args.dts, args.integrator,
+                                    args.seed, args.therm, args.therm_tau, args.therm_dt):
             print(json.dumps(rec), flush=True)
         return
     for rec in dh_study(tuple(args.dims), args.tau, args.dts, args.integrator, args.precisions,
