@@ -17,7 +17,8 @@ exchange step on one lattice per GPU); value = links of all ranks / max time.
 --profile-force WORKLOAD runs only W + K FP32 force calls (the staple-field
 force with the fused momentum step and action) on that workload (a key of
 synth.WORKLOADS, e.g. 16^3x32) and prints their mean time: the small case
-that profiler captures run.
+that profiler captures run.  --profile-wilson WORKLOAD does the same for the
+FP32 Wilson hopping operator and hopping-term force.
 """
 from __future__ import annotations
 
@@ -739,6 +740,41 @@ def run_profile_force(args):
     return 0
 
 
+def run_profile_wilson(args):
+    """W + K launches each of the FP32 Wilson hopping operator (Y = X -
+    kappa calD X) and of the hopping-term force with the fused momentum step
+    on one workload, for profiler captures; prints their mean times."""
+    import torch
+
+    from paper_1808_02281_gb300 import build as B
+    from paper_1808_02281_gb300 import lqcd, synth
+
+    B.build()
+    w = synth.WORKLOADS[args.profile_wilson]
+    dims = w["dims"]
+    lat = lqcd.Lattice(dims, "f32")
+    U = lqcd.links_from_omega(lat, lqcd.algebra_to_device(lat, synth.omega(dims, w["sigma"], w["seed"])))
+    X = lqcd.spinor_to_device(lat, synth.spinor(dims, 11))
+    Y = lqcd.empty_spinor(lat)
+    pm = lqcd.algebra_to_device(lat, synth.momenta(dims, seed=1000 + w["seed"]))
+    out = {"profile_wilson": args.profile_wilson, "sites": lat.V}
+    for name, fn in (("dslash", lambda: lqcd.wilson_dslash(lat, U, X, 1.0, -WILSON_KAPPA, out=Y)),
+                     ("force", lambda: lqcd.wilson_hopping_force(lat, U, X, Y, coef=WILSON_KAPPA,
+                                                                mom=pm, dt=DT))):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.steps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        out[name + "_ms"] = a.elapsed_time(b) / args.steps
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -750,11 +786,15 @@ def main():
                          "at set-up; -1 (default) autotunes")
     ap.add_argument("--profile-force", default=None, metavar="WORKLOAD",
                     help="only time FP32 force calls on this workload (profiler captures)")
+    ap.add_argument("--profile-wilson", default=None, metavar="WORKLOAD",
+                    help="only time the FP32 Wilson kernels on this workload (profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.profile_force:
         return run_profile_force(args)
+    if args.profile_wilson:
+        return run_profile_wilson(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -109,13 +109,9 @@ template <typename R> struct Planes<R, false> {
 
     __device__ __forceinline__ Ref at(int n) const { return n; }
 
-    template <bool COH = false> __device__ __forceinline__ Mat<R> load(Ref n, int plane) const
-    {
-        static_assert(!COH, "compact planes are only read-only fields");
-        return load_link(sf, V, plane, n);
-    }
+    __device__ __forceinline__ Mat<R> load(Ref n, int plane) const { return load_link(sf, V, plane, n); }
 
-    template <bool STREAM = true> __device__ __forceinline__ void store(Ref n, int plane, const Mat<R> &u) const
+    __device__ __forceinline__ void store(Ref n, int plane, const Mat<R> &u) const
     {
         store_link(sf, V, plane, n, u);
     }
@@ -140,16 +136,14 @@ template <typename R> struct Planes<R, true> {
         return Ref{b + s * 16, b + B::NW * B::LANE + s * 8};
     }
 
-    // COH: a coherent load (planes written by other blocks of the same
-    // launch, read after an acquire), else the read-only path.
-    template <bool COH = false> __device__ __forceinline__ Mat<R> load(const Ref &r, int plane) const
+    __device__ __forceinline__ Mat<R> load(const Ref &r, int plane) const
     {
         const int64_t off = (int64_t)plane * plane_bytes;
         const V4 *p = reinterpret_cast<const V4 *>(r.p + off);
         R x[18];
 #pragma unroll
         for (int q = 0; q < B::NW; ++q) {
-            const V4 v = COH ? __ldca(p + q * (B::LANE / 16)) : __ldg(p + q * (B::LANE / 16));
+            const V4 v = __ldg(p + q * (B::LANE / 16));
             if constexpr (B::W == 4) {
                 x[4 * q + 0] = v.x;
                 x[4 * q + 1] = v.y;
@@ -161,8 +155,7 @@ template <typename R> struct Planes<R, true> {
             }
         }
         if constexpr (B::TAIL == 2) {
-            const float2 *tp = reinterpret_cast<const float2 *>(r.t + off);
-            const float2 t = COH ? __ldca(tp) : __ldg(tp);
+            const float2 t = __ldg(reinterpret_cast<const float2 *>(r.t + off));
             x[16] = t.x;
             x[17] = t.y;
         }
@@ -177,9 +170,6 @@ template <typename R> struct Planes<R, true> {
         return u;
     }
 
-    // STREAM: evict-first stores (a field read back after the pass), else
-    // plain stores (data that should stay in L2).
-    template <bool STREAM = true>
     __device__ __forceinline__ void store(const Ref &r, int plane, const Mat<R> &u) const
     {
         const int64_t off = (int64_t)plane * plane_bytes;
@@ -197,14 +187,9 @@ template <typename R> struct Planes<R, true> {
             V4 v;
             if constexpr (B::W == 4) v = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
             else v = make_double2(x[2 * q], x[2 * q + 1]);
-            if constexpr (STREAM) __stcs(p + q * (B::LANE / 16), v);
-            else p[q * (B::LANE / 16)] = v;
+            __stcs(p + q * (B::LANE / 16), v);
         }
-        if constexpr (B::TAIL == 2) {
-            float2 *tp = reinterpret_cast<float2 *>(r.t + off);
-            if constexpr (STREAM) __stcs(tp, make_float2(x[16], x[17]));
-            else *tp = make_float2(x[16], x[17]);
-        }
+        if constexpr (B::TAIL == 2) __stcs(reinterpret_cast<float2 *>(r.t + off), make_float2(x[16], x[17]));
     }
 };
 
@@ -366,7 +351,7 @@ __device__ __forceinline__ int batch_entry(const SfBatch &B, int64_t vb)
 
 // The six staples S^{(mu)}_b, b = +-nu (nu != mu), of the link (x, mu), x
 // at coordinates c; stored at staple index sx of sf.
-template <typename R, bool FULL, bool STREAM>
+template <typename R, bool FULL>
 __device__ __forceinline__ void site_staples(const R *__restrict__ links, const G32 &g, const Coord &c,
                                              int x, int mu, const Planes<R, FULL> &sf, int sx)
 {
@@ -384,12 +369,12 @@ __device__ __forceinline__ void site_staples(const R *__restrict__ links, const 
         Mat<R> t = mul<N, D>(load_link(links, V, nu, xm), load_link(links, V, mu, x + vp));
         Mat<R> up = mul_top2<N, D>(t, load_link(links, V, nu, x));
         if constexpr (FULL) rebuild_row2(up);
-        sf.template store<STREAM>(at, mu * 6 + 2 * iv, up);
+        sf.store(at, mu * 6 + 2 * iv, up);
         // b = -nu:  U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu)
         t = mul<D, D>(load_link(links, V, nu, xm + vm), load_link(links, V, mu, x + vm));
         Mat<R> dn = mul_top2<N, N>(t, load_link(links, V, nu, x + vm));
         if constexpr (FULL) rebuild_row2(dn);
-        sf.template store<STREAM>(at, mu * 6 + 2 * iv + 1, dn);
+        sf.store(at, mu * 6 + 2 * iv + 1, dn);
     }
 }
 
@@ -400,7 +385,7 @@ __device__ __forceinline__ void staples_block(const SfLattice &L, const G32 &g, 
     const int mu = (int)(threadIdx.x >> 5);
     const int x = vb * 32 + (int)(threadIdx.x & 31);
     if (x >= g.V) return;
-    site_staples<R, FULL, true>(static_cast<const R *>(L.links), g, coord32(g, x), x, mu,
+    site_staples<R, FULL>(static_cast<const R *>(L.links), g, coord32(g, x), x, mu,
                                 planes_of<R, FULL>(L), x);
 }
 
@@ -439,10 +424,8 @@ __device__ __forceinline__ void acc_su3(Mat<R> &y, const Mat<R> &a, const Mat<R>
     else mul_acc_su3<FB>(y, a, b, s);
 }
 
-// Where the staples of a site and of its neighbours are stored.  In the
-// lattice-wide staple field (LatticeSites) that is the site index itself;
-// in the ring of the fused schedule it is a slot of halo'd slices
-// (RingSites, below).
+// Where the staples of a site and of its neighbours are stored: in the
+// lattice-wide staple field, the site index itself.
 struct LatticeSites {
     const G32 *g;
     const Coord *c;
@@ -455,7 +438,7 @@ struct LatticeSites {
 //   t += B_d [ c_cube sum_{b perp rho, d} S_b(k+d) S^{(d)}_b(k) + c_rect S_d(k+d) A_d^dag ]
 // (the orientation of the shared links fixed at compile time, so that each
 // sign has one small loop body).
-template <bool NEG, bool UNROLLQ, bool FULL, bool DIRECT, bool COH, typename R, typename SI>
+template <bool NEG, bool UNROLLQ, bool FULL, bool DIRECT, typename R, typename SI>
 __device__ __forceinline__ void d_terms(Mat<R> &t, const R *__restrict__ links,
                                         const Planes<R, FULL> &sf, const SI &si, const G32 &g,
                                         const Coord &c, int rho, int k, int kp, int id, R c_rt,
@@ -478,12 +461,12 @@ __device__ __forceinline__ void d_terms(Mat<R> &t, const R *__restrict__ links,
         const int ib = q == 0 ? (id == 0 ? 1 : 0) : (id == 2 ? 1 : 2);
         const int nub = (rho + 1 + ib) & 3;
         const int jp = 2 * ((nub - nud - 1) & 3);
-        acc_su3<FD, DIRECT>(y, sf.template load<COH>(at_d, base + 2 * ib),
-                            sf.template load<COH>(at_2, nud * 6 + jp), c_cb);
-        acc_su3<FD, DIRECT>(y, sf.template load<COH>(at_d, base + 2 * ib + 1),
-                            sf.template load<COH>(at_2, nud * 6 + jp + 1), c_cb);
+        acc_su3<FD, DIRECT>(y, sf.load(at_d, base + 2 * ib),
+                            sf.load(at_2, nud * 6 + jp), c_cb);
+        acc_su3<FD, DIRECT>(y, sf.load(at_d, base + 2 * ib + 1),
+                            sf.load(at_2, nud * 6 + jp + 1), c_cb);
     }
-    Mat<R> r3 = sf.template load<COH>(at_d, base + jd);
+    Mat<R> r3 = sf.load(at_d, base + jd);
     if constexpr (DIRECT) {
         scale(y, c_cb);
         scale(r3, c_rt);
@@ -499,7 +482,7 @@ __device__ __forceinline__ void d_terms(Mat<R> &t, const R *__restrict__ links,
 
 // Force (and the fused momentum step) on the link (k, rho), k at coordinates
 // c, its staples found through si; returns its share of the action.
-template <typename R, bool ACTION, bool UNROLLQ, bool FULL, bool DIRECT, bool COH, typename SI>
+template <typename R, bool ACTION, bool UNROLLQ, bool FULL, bool DIRECT, typename SI>
 __device__ __forceinline__ double force_link(const SfLattice &L, const KernelScalars &sc, const G32 &g,
                                              const Planes<R, FULL> &sf, const SI &si, const Coord &c,
                                              int k, int rho)
@@ -521,10 +504,10 @@ __device__ __forceinline__ double force_link(const SfLattice &L, const KernelSca
         const auto at_k = sf.at(si.at0()), at_p = sf.at(si.nb(rho, 1)), at_m = sf.at(si.nb(rho, -1));
 #pragma unroll 1
         for (int jj = 0; jj < 6; ++jj) {
-            const Mat<R> s = sf.template load<COH>(at_k, base + jj);
+            const Mat<R> s = sf.load(at_k, base + jj);
             add_to(pl, s);
-            acc_su3<N, DIRECT>(p1, sf.template load<COH>(at_p, base + jj), s, c_rt);
-            mul_acc<N, N>(p2, s, sf.template load<COH>(at_m, base + jj));
+            acc_su3<N, DIRECT>(p1, sf.load(at_p, base + jj), s, c_rt);
+            mul_acc<N, N>(p2, s, sf.load(at_m, base + jj));
         }
         if constexpr (ACTION) tr_pl = re_trace_mul<N, N>(load_link(links, V, rho, k), pl);
         t = pl;
@@ -537,10 +520,10 @@ __device__ __forceinline__ double force_link(const SfLattice &L, const KernelSca
     // cubes and the rectangles along d: positive, then negative d
 #pragma unroll 1
     for (int id = 0; id < 3; ++id)
-        d_terms<false, UNROLLQ, FULL, DIRECT, COH>(t, links, sf, si, g, c, rho, k, kp, id, c_rt, c_cb);
+        d_terms<false, UNROLLQ, FULL, DIRECT>(t, links, sf, si, g, c, rho, k, kp, id, c_rt, c_cb);
 #pragma unroll 1
     for (int id = 0; id < 3; ++id)
-        d_terms<true, UNROLLQ, FULL, DIRECT, COH>(t, links, sf, si, g, c, rho, k, kp, id, c_rt, c_cb);
+        d_terms<true, UNROLLQ, FULL, DIRECT>(t, links, sf, si, g, c, rho, k, kp, id, c_rt, c_cb);
 
     const Mat<R> m = mul<N, N>(load_link(links, V, rho, k), t);
     R f[8];
@@ -575,8 +558,8 @@ __device__ __forceinline__ double force_block(const SfLattice &L, const KernelSc
     const Coord c = swept_site(sw, j);
     const int k = index32(g, c);
     const LatticeSites si{&g, &c, k};
-    return force_link<R, ACTION, UNROLLQ, FULL, DIRECT, false>(L, sc, g, planes_of<R, FULL>(L), si, c,
-                                                               k, rho);
+    return force_link<R, ACTION, UNROLLQ, FULL, DIRECT>(L, sc, g, planes_of<R, FULL>(L), si, c, k,
+                                                        rho);
 }
 
 // Resident CTAs per SM the register allocation aims at: 4 (128 registers)
@@ -626,226 +609,6 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<R, ACTION, DENSE>()))
     }
 }
 
-// ------------------------------------------------------------ fused schedule
-//
-// The staples of the lattice never go to HBM: the lattice is cut into
-// spatial blocks of whole x rows (by x bz rows), and each block is swept
-// along t.  "A" items compute the staples of one t-slice of a block and of
-// its y/z halo of one row into a ring of R slots that stays in L2; "B"
-// items compute the force on one slice of the block from the three slices
-// t-1, t, t+1 of the ring.  Items are handed out in a fixed order from a
-// work counter (per block: A(t=-1), A(0), then A(t+1), B(t) for t = 0 ..
-// L3-1; the slices -1 and L3 are the periodic images L3-1 and 0, computed
-// again into their own slots), and an item waits only for items handed out
-// before it: a B item for the three A slices it reads, an A item for the B
-// items that read the slot's previous slice.  Every resident block works
-// on the lowest unfinished items, so the waits always end; each is bounded
-// anyway (after about two seconds the item sets an error word, the action
-// comes out NaN, and the launch still ends).  The halo rows are computed
-// twice (by the neighbouring blocks too): 1 + 2/by + 2/bz + 4/(by bz) times
-// the staple work, in exchange for staples that are written to and read
-// from L2 only.
-
-// The fused schedule's geometry and buffers (filled on the host).
-struct Ring {
-    int by, bz;          // rows of a spatial block along y, z (blocks hold whole x rows)
-    int nby, nbz;        // blocks along y, z
-    int ry;              // halo'd rows along y (by + 2)
-    int nring;           // sites of one slot: L0 (by + 2) (bz + 2)
-    int R;               // slots
-    int nA, nB;          // virtual blocks of an A slice and of a B slice
-    int per_block;       // items of one block: 2 nA + L3 (nA + nB)
-    int nslices;         // slices of all blocks: blocks (L3 + 2)
-    int64_t total;       // items of the launch
-    int *a_done;         // per slice: A items finished
-    int *b_done;         // per slice, as the centre of B items: B items finished
-    unsigned long long *work; // item counter
-    unsigned int *error; // set when a wait ran out
-    char *ring;          // staple planes of the R slots (full form)
-    int64_t plane_bytes;
-};
-
-struct RingSites {
-    const Ring *r;
-    int L0, x, yr, zr, slot;
-    __device__ __forceinline__ int idx(int x_, int yr_, int zr_, int slot_) const
-    {
-        return slot_ * r->nring + (zr_ * r->ry + yr_) * L0 + x_;
-    }
-    __device__ __forceinline__ int at0() const { return idx(x, yr, zr, slot); }
-    __device__ __forceinline__ int nb(int mu, int s) const
-    {
-        if (mu == 0) {
-            const int x2 = x + s;
-            return idx(x2 < 0 ? L0 - 1 : (x2 == L0 ? 0 : x2), yr, zr, slot);
-        }
-        if (mu == 1) return idx(x, yr + s, zr, slot);
-        if (mu == 2) return idx(x, yr, zr + s, slot);
-        const int s2 = slot + s;
-        return idx(x, yr, zr, s2 < 0 ? r->R - 1 : (s2 == r->R ? 0 : s2));
-    }
-};
-
-constexpr int kWaitPolls = 1 << 25;             // hard bound on the polls of one wait
-constexpr unsigned long long kWaitNs = 2000000000ull; // and on its duration
-
-// Polls use relaxed loads: an acquire also discards the SM's L1 contents,
-// which the other blocks on the SM are using; one acquire fence follows
-// once the counts are reached.
-__device__ __forceinline__ int load_relaxed(const int *p)
-{
-    int v;
-    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Thread 0 waits until *ctr >= target (bounded; on a timeout the error word
-// is set and the item goes on; once the word is set no wait of the launch
-// waits any more, so a launch that went wrong still ends promptly).
-__device__ __forceinline__ void wait_count(const int *ctr, int target, unsigned int *error)
-{
-    if (load_relaxed(ctr) < target) {
-        const volatile unsigned int *err = error;
-        const unsigned long long t0 = global_ns();
-        int i = 0;
-        for (; i < kWaitPolls; ++i) {
-            if (*err != 0u) return;
-            __nanosleep(128);
-            if (load_relaxed(ctr) >= target) break;
-            if ((i & 255) == 255 && global_ns() - t0 > kWaitNs) {
-                i = kWaitPolls;
-                break;
-            }
-        }
-        if (i == kWaitPolls) atomicOr(error, 1u);
-    }
-}
-
-// After the relaxed polls of an item's waits: the acquire that orders the
-// block's following reads after the producers' writes (one per item).
-__device__ __forceinline__ void acquire_fence()
-{
-    asm volatile("fence.acq_rel.gpu;" ::: "memory");
-}
-
-// Is global slice c the centre of a B slice (and not a block's halo slice)?
-__device__ __forceinline__ bool b_centre(const Ring &F, int L3, int c)
-{
-    if (c < 0 || c >= F.nslices) return false;
-    const int s = c % (L3 + 2);
-    return s >= 1 && s <= L3;
-}
-
-template <typename R, bool ACTION>
-__global__ void __launch_bounds__(kBlock, (min_blocks<R, ACTION, true>()))
-    force_fused(const __grid_constant__ SfLattice L, const __grid_constant__ KernelScalars sc,
-                const __grid_constant__ Ring F)
-{
-    const G32 g = make_g32(L.dims);
-    const Planes<R, true> ring{F.ring, F.plane_bytes};
-    const int w = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
-    for (int64_t it = next_virtual_block(F.work); it < F.total; it = next_virtual_block(F.work)) {
-        const int b = (int)(it / F.per_block);
-        int i = (int)(it - (int64_t)b * F.per_block);
-        bool is_a;
-        int sl, vb; // local slice (t + 1) and virtual block within the slice
-        if (i < 2 * F.nA) {
-            is_a = true;
-            sl = i / F.nA;
-            vb = i - sl * F.nA;
-        } else {
-            i -= 2 * F.nA;
-            const int pair = i / (F.nA + F.nB), r = i - pair * (F.nA + F.nB);
-            is_a = r < F.nA;
-            sl = is_a ? pair + 2 : pair + 1;
-            vb = is_a ? r : r - F.nA;
-        }
-        const int gs = b * (g.L3 + 2) + sl;
-        const int slot = gs % F.R;
-        const int by0 = (b % F.nby) * F.by, bz0 = (b / F.nby) * F.bz;
-        if (is_a) {
-            // the slot's previous slice must have been read by all its B items
-            if (threadIdx.x == 0) {
-                for (int c = gs - F.R - 1; c <= gs - F.R + 1; ++c)
-                    if (b_centre(F, g.L3, c)) wait_count(F.b_done + c, F.nB, F.error);
-                acquire_fence();
-            }
-            __syncthreads();
-            const int rr = vb * 32 + lane;
-            if (rr < F.nring) {
-                Coord c;
-                c.c0 = rr % g.L0;
-                const int q = rr / g.L0, yr = q % F.ry, zr = q / F.ry;
-                c.c1 = ((by0 + yr - 1) % g.L1 + g.L1) % g.L1;
-                c.c2 = ((bz0 + zr - 1) % g.L2 + g.L2) % g.L2;
-                c.c3 = ((sl - 1) % g.L3 + g.L3) % g.L3;
-                site_staples<R, true, false>(static_cast<const R *>(L.links), g, c, index32(g, c), w,
-                                             ring, slot * F.nring + rr);
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                __threadfence();
-                atomicAdd(F.a_done + gs, 1);
-            }
-        } else {
-            if (threadIdx.x == 0) {
-                for (int c = gs - 1; c <= gs + 1; ++c) wait_count(F.a_done + c, F.nA, F.error);
-                acquire_fence();
-            }
-            __syncthreads();
-            const int t = sl - 1;
-            const int ii = vb * 32 + lane;
-            double acc = 0.0;
-            if (ii < g.L0 * F.by * F.bz) {
-                const int x = ii % g.L0, q = ii / g.L0, y = q % F.by, z = q / F.by;
-                const Coord c{x, by0 + y, bz0 + z, t};
-                const int k = index32(g, c);
-                const RingSites si{&F, g.L0, x, y + 1, z + 1, slot};
-                acc = force_link<R, ACTION, false, true, direct_default<R, true>(), true>(
-                    L, sc, g, ring, si, c, k, w);
-            }
-            if constexpr (ACTION) {
-                const double s = block_sum(acc);
-                if (threadIdx.x == 0) L.partials[((int64_t)b * g.L3 + t) * F.nB + vb] = s;
-            } else {
-                __syncthreads();
-            }
-            if (threadIdx.x == 0) {
-                __threadfence(); // the block's reads of the ring come before the release
-                atomicAdd(F.b_done + gs, 1);
-            }
-        }
-    }
-}
-
-// The action from the fused schedule's partial sums (fixed order), NaN if a
-// wait of the launch ran out.
-__global__ void __launch_bounds__(1024) finish_fused(const double *partials, int count, double scale,
-                                                     const unsigned int *error, double *out)
-{
-    __shared__ double warp_part[32];
-    double v = 0.0;
-    for (int i = threadIdx.x; i < count; i += 1024) v += partials[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) warp_part[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        double s = warp_part[lane];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) *out = *error != 0u ? __longlong_as_double(0x7ff8000000000000ll) : scale * s;
-    }
-}
-
 // One block per lattice of a batch: its action from its partial sums, in the
 // order and grouping of finish_sum, so batched and single results agree.
 __global__ void __launch_bounds__(1024) finish_batched(const __grid_constant__ SfBatch B, double scale)
@@ -887,20 +650,17 @@ unsigned grid_of(int64_t items)
 //      4.45 ms with 64x16x16 at 32^3x64 FP32)
 //   5  as 4, registers capped for 4 CTAs/SM
 //   6  as 4 with spatial blocks up to 64x16x16
-//   7  fused: no lattice-wide staple field; the staples of each t-slice of a
-//      spatial block (with a halo row) are computed into an L2-resident
-//      ring just ahead of the force items that read them (one launch)
 // The process-wide choice per precision is set by lqcd_set_force_variant or
 // lqcd_autotune_force; -1 means the default: x rows with full staples, in
 // FP32 with the 4-CTA register cap (at 32^3x64: FP32 3.62 ms, 3.65 uncapped,
 // 4.28 with compact staples; FP64 110 vs 128 ms).
-constexpr int kSfVariants = 8;
+constexpr int kSfVariants = 7;
 
 bool full_staples(int variant) { return variant >= 4; }
 
 // Slot of a kernel instance in the occupancy cache of persistent_grid:
 // kind (0 pass B, 1 pass B capped, 2 pass B full, 3 pass B full capped,
-// 4 pass A compact, 5 pass A full, 6 fused) x precision x action x unrolled.
+// 4 pass A compact, 5 pass A full) x precision x action x unrolled.
 int grid_slot(int kind, bool f64, bool action, bool unrolled)
 {
     return kind * 8 + (f64 ? 4 : 0) + (action ? 2 : 0) + (unrolled ? 1 : 0);
@@ -918,7 +678,7 @@ int block_extent(int L, int cap)
 
 void set_traversal(SfLattice &L, int variant)
 {
-    const int cap_yz = (variant == 4 || variant == 5 || variant == 7) ? 8 : 16;
+    const int cap_yz = (variant == 4 || variant == 5) ? 8 : 16;
     L.sweep[0] = block_extent(L.dims[0], 64);
     L.sweep[1] = block_extent(L.dims[1], cap_yz);
     L.sweep[2] = block_extent(L.dims[2], cap_yz);
@@ -1004,7 +764,7 @@ cudaError_t launch_pass_b_batched(const SfBatch &B, const KernelScalars &sc, int
     } else if (variant == 4 || variant == 6) {
         auto k = force_from_staples_batched<R, ACTION, false, false, true>;
         k<<<persistent_grid(k, grid_slot(2, f64, ACTION, false), B.total), kBlock, 0, st>>>(B, sc);
-    } else if (variant == 5 || variant == 7) { // the fused schedule is single-lattice only
+    } else if (variant == 5) {
         auto k = force_from_staples_batched<R, ACTION, false, true, true>;
         k<<<persistent_grid(k, grid_slot(3, f64, ACTION, false), B.total), kBlock, 0, st>>>(B, sc);
 
@@ -1015,96 +775,11 @@ cudaError_t launch_pass_b_batched(const SfBatch &B, const KernelScalars &sc, int
     return cudaGetLastError();
 }
 
-// Geometry of the fused schedule: spatial blocks of up to 8 x 8 rows, fewer
-// where one slot would pass 6 MB (six slots then take at most 36 MB of L2).
-Ring ring_shape(const int dims[4], int precision)
-{
-    const size_t site_bytes = (size_t)kStaplePlanes * 18 * (precision == LQCD_F64 ? 8 : 4);
-    const size_t cap = (size_t)6 << 20;
-    int by = block_extent(dims[1], 8), bz = block_extent(dims[2], 8);
-    while ((size_t)dims[0] * (by + 2) * (bz + 2) * site_bytes > cap && (by > 1 || bz > 1)) {
-        if (by >= bz) by = block_extent(dims[1], by - 1);
-        else bz = block_extent(dims[2], bz - 1);
-    }
-    Ring F{};
-    F.by = by;
-    F.bz = bz;
-    F.nby = dims[1] / by;
-    F.nbz = dims[2] / bz;
-    F.ry = by + 2;
-    F.nring = dims[0] * (by + 2) * (bz + 2);
-    F.R = 6;
-    F.nA = (F.nring + 31) / 32;
-    F.nB = (dims[0] * by * bz + 31) / 32;
-    F.per_block = 2 * F.nA + dims[3] * (F.nA + F.nB);
-    F.nslices = F.nby * F.nbz * (dims[3] + 2);
-    F.total = (int64_t)F.nby * F.nbz * F.per_block;
-    return F;
-}
-
 size_t round_up256(size_t b) { return (b + 255) & ~(size_t)255; }
-
-// Workspace of the fused schedule, from its start: the ring's planes, the
-// two counter arrays, the item counter and the error word.
-size_t fused_ring_bytes(const Ring &F, int precision)
-{
-    return round_up256((size_t)kStaplePlanes * full_plane_bytes((int64_t)F.R * F.nring, precision));
-}
-
-size_t fused_bytes(const int dims[4], int precision)
-{
-    const Ring F = ring_shape(dims, precision);
-    return fused_ring_bytes(F, precision) + round_up256(2 * (size_t)F.nslices * sizeof(int)) + 256;
-}
-
-int fused_partials(const int dims[4])
-{
-    const Ring F = ring_shape(dims, LQCD_F32); // the block shape does not change the count much
-    const Ring G = ring_shape(dims, LQCD_F64);
-    const int64_t a = (int64_t)F.nby * F.nbz * dims[3] * F.nB, b = (int64_t)G.nby * G.nbz * dims[3] * G.nB;
-    return (int)(a > b ? a : b);
-}
-
-template <typename R> cudaError_t launch_fused_t(const ForceArgs &a, const KernelScalars &sc, cudaStream_t st)
-{
-    SfLattice L{};
-    for (int i = 0; i < 4; ++i) L.dims[i] = a.dims[i];
-    L.links = a.links;
-    L.force = a.force;
-    L.mom = a.mom;
-    L.partials = a.partials;
-    L.action = a.action;
-    Ring F = ring_shape(a.dims, a.precision);
-    char *ws = static_cast<char *>(a.staples);
-    F.ring = ws;
-    F.plane_bytes = (int64_t)full_plane_bytes((int64_t)F.R * F.nring, a.precision);
-    char *ctr = ws + fused_ring_bytes(F, a.precision);
-    F.a_done = reinterpret_cast<int *>(ctr);
-    F.b_done = F.a_done + F.nslices;
-    char *tail = ctr + round_up256(2 * (size_t)F.nslices * sizeof(int));
-    F.work = reinterpret_cast<unsigned long long *>(tail);
-    F.error = reinterpret_cast<unsigned int *>(tail + 8);
-    cudaError_t e = cudaMemsetAsync(ctr, 0, (size_t)(tail + 16 - ctr), st);
-    if (e != cudaSuccess) return e;
-    constexpr bool f64 = sizeof(R) == 8;
-    if (a.action != nullptr) {
-        auto k = force_fused<R, true>;
-        k<<<persistent_grid(k, grid_slot(6, f64, true, false), F.total), kBlock, 0, st>>>(L, sc, F);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        const int count = (int)((int64_t)F.nby * F.nbz * a.dims[3] * F.nB);
-        finish_fused<<<1, 1024, 0, st>>>(a.partials, count, a.beta / 3.0, F.error, a.action);
-    } else {
-        auto k = force_fused<R, false>;
-        k<<<persistent_grid(k, grid_slot(6, f64, false, false), F.total), kBlock, 0, st>>>(L, sc, F);
-    }
-    return cudaGetLastError();
-}
 
 template <typename R> cudaError_t launch_sf_t(const ForceArgs &a, cudaStream_t st)
 {
     const int variant = resolve_variant(a);
-    if (variant == 7) return launch_fused_t<R>(a, make_scalars(a), st);
     SfLattice L{};
     for (int i = 0; i < 4; ++i) L.dims[i] = a.dims[i];
     set_traversal(L, variant);
@@ -1179,9 +854,7 @@ cudaError_t launch_sf_batched_t(const ForceArgs &a, int n, const SfLattice *item
 size_t staple_field_bytes(const int dims[4], int precision)
 {
     const int64_t V = (int64_t)dims[0] * dims[1] * dims[2] * dims[3];
-    const size_t two_pass = round_up256((size_t)kStaplePlanes * full_plane_bytes(V, precision));
-    const size_t fused = fused_bytes(dims, precision);
-    return two_pass > fused ? two_pass : fused;
+    return round_up256((size_t)kStaplePlanes * full_plane_bytes(V, precision));
 }
 
 bool staple_fields_supported(const int dims[4])
@@ -1191,9 +864,7 @@ bool staple_fields_supported(const int dims[4])
 
 int staple_force_partials(const int dims[4])
 {
-    const int a = (int)virtual_blocks((int64_t)dims[0] * dims[1] * dims[2] * dims[3]);
-    const int b = fused_partials(dims);
-    return a > b ? a : b;
+    return (int)virtual_blocks((int64_t)dims[0] * dims[1] * dims[2] * dims[3]);
 }
 
 cudaError_t launch_force_staple_fields(const ForceArgs &a, cudaStream_t st)

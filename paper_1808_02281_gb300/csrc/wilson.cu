@@ -227,6 +227,45 @@ __device__ __forceinline__ void hop(Spinor<R> &acc, const R *__restrict__ links,
     accumulate<MU, +1>(acc, colour_mul<D>(load_link(links, g.V, MU, nb), project<MU, +1>(load_spinor(x, g.V, nb))));
 }
 
+// The x hops from the lanes of the same warp, when a warp holds whole x
+// rows (the x extent divides 32; lanes n and n +- x are then lanes of one
+// row of L0 lanes, with periodic wrap inside the row).  Each lane projects
+// its own spinor both ways, keeps (1 - gamma_x) x_n for lane n-1's forward
+// hop and applies its own link's dagger to (1 + gamma_x) x_n for lane n+1's
+// backward hop (U_{n,x} is the backward link of site n+x), so that lane n
+// receives 2 x 12 reals by shuffles instead of loading two neighbour
+// spinors and the backward link (15 of the 78 16-byte loads of a site).
+template <typename R> __device__ __forceinline__ R shfl_row(R v, int src)
+{
+    return __shfl_sync(0xffffffffu, v, src);
+}
+
+template <typename R> __device__ __forceinline__ Half<R> shfl_half(const Half<R> &h, int src)
+{
+    Half<R> r;
+#pragma unroll
+    for (int al = 0; al < 2; ++al)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            r.re[al][a] = shfl_row(h.re[al][a], src);
+            r.im[al][a] = shfl_row(h.im[al][a], src);
+        }
+    return r;
+}
+
+template <typename R>
+__device__ __forceinline__ void hop_x_shuffled(Spinor<R> &acc, const R *__restrict__ links,
+                                               const Spinor<R> &xn, int64_t V, int64_t n, int L0)
+{
+    const int lane = (int)(threadIdx.x & 31), m = L0 - 1;
+    const int up = (lane & ~m) | ((lane + 1) & m), dn = (lane & ~m) | ((lane - 1) & m);
+    const Mat<R> u = load_link(links, V, 0, n);
+    const Half<R> fw = shfl_half(project<0, -1>(xn), up);                  // (1 - g_x) x_{n+x}
+    const Half<R> bw = shfl_half(colour_mul<D>(u, project<0, +1>(xn)), dn); // U_{n-x}^dag (1 + g_x) x_{n-x}
+    accumulate<0, -1>(acc, colour_mul<N>(u, fw));
+    accumulate<0, +1>(acc, bw);
+}
+
 constexpr int kDslashBlock = 128;
 
 // Register cap: 4 blocks (16 warps) per SM in FP32, measured 17 % faster at
@@ -235,7 +274,8 @@ constexpr int kDslashBlock = 128;
 template <typename R> constexpr int dslash_min_blocks() { return sizeof(R) == 8 ? 1 : 4; }
 
 // out_n = ca x_n + cb (calD x)_n, one thread per site.
-template <typename R>
+// XSHFL: x hops by shuffles.
+template <typename R, bool XSHFL>
 __global__ void __launch_bounds__(kDslashBlock, dslash_min_blocks<R>())
     wilson_dslash(const __grid_constant__ WilsonArgs a)
 {
@@ -253,7 +293,12 @@ __global__ void __launch_bounds__(kDslashBlock, dslash_min_blocks<R>())
         for (int al = 0; al < 4; ++al)
 #pragma unroll
             for (int b = 0; b < 3; ++b) acc.re[al][b] = acc.im[al][b] = R(0);
-        hop<0>(acc, links, x, g, c, n);
+        if constexpr (XSHFL) {
+            const Spinor<R> xn = load_spinor(x, g.V, n);
+            hop_x_shuffled(acc, links, xn, g.V, n, g.L0);
+        } else {
+            hop<0>(acc, links, x, g, c, n);
+        }
         hop<1>(acc, links, x, g, c, n);
         hop<2>(acc, links, x, g, c, n);
         hop<3>(acc, links, x, g, c, n);
@@ -361,8 +406,18 @@ cudaError_t launch_wilson_dslash(const WilsonArgs &args, cudaStream_t st)
     const WilsonArgs a = with_float_scalars(args);
     const int64_t V = (int64_t)a.dims[0] * a.dims[1] * a.dims[2] * a.dims[3];
     const unsigned grid = blocks_for(V, kDslashBlock);
-    if (a.precision == LQCD_F64) wilson_dslash<double><<<grid, kDslashBlock, 0, st>>>(a);
-    else wilson_dslash<float><<<grid, kDslashBlock, 0, st>>>(a);
+    // shuffled x hops need whole x rows in every warp: L0 divides 32 (then
+    // V is a multiple of L0 and every warp's first site starts a row), and a
+    // grid-stride loop that never runs a warp past V with only part of it
+    const int L0 = a.dims[0];
+    const bool xshfl = L0 <= 32 && (32 % L0) == 0 && V % 32 == 0 &&
+                       (int64_t)grid * kDslashBlock >= V;
+    if (a.precision == LQCD_F64) { // FP64-pipe bound; the shuffled form spills there
+        wilson_dslash<double, false><<<grid, kDslashBlock, 0, st>>>(a);
+    } else {
+        if (xshfl) wilson_dslash<float, true><<<grid, kDslashBlock, 0, st>>>(a);
+        else wilson_dslash<float, false><<<grid, kDslashBlock, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -30,6 +30,9 @@ CASES = [
     ((1, 2, 3, 4), 0.6),      # degenerate extents: x + mu = x and x + mu = x - mu
     ((8, 8, 8, 16), 0.3),     # 256 blocks of the force kernel
     ((6, 10, 6, 14), 0.15),   # near-unit links (the spread of the 16^3x32 workload)
+    # x extent dividing 32: the operator's x hops by warp shuffles (FP32)
+    ((32, 4, 2, 3), 0.4),     # one x row per warp
+    ((16, 4, 4, 4), 0.4),     # two x rows per warp
 ]
 
 
