@@ -67,6 +67,7 @@ CASES = [
     ((2, 3, 2, 5), 0.4, 0.87),       # extent 2: +-2 displacements coincide
     ((5, 1, 3, 2), 0.4, 0.87),       # extent 1 in one direction
     ((1, 1, 1, 1), 0.6, 0.87),       # a single site: every loop wraps onto itself
+    ((8, 6, 12, 4), 0.4, 0.87),      # sweep blocks of 8x6x6: two z blocks, extents not powers of 2
 ]
 
 
