@@ -782,7 +782,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--force-variant", type=int, default=-1,
-                    help="fix the staple-field force schedule (0..7) instead of autotuning it "
+                    help="fix the staple-field force schedule (0..6) instead of autotuning it "
                          "at set-up; -1 (default) autotunes")
     ap.add_argument("--profile-force", default=None, metavar="WORKLOAD",
                     help="only time FP32 force calls on this workload (profiler captures)")

@@ -8,7 +8,7 @@
 // of 4.  It is a product of three SU(3) matrices, so it is SU(3): its first
 // two rows (which need only two rows of the first product) determine the
 // third, conj(row0 x row1).  Planes are stored compact (two rows, the third
-// rebuilt on load, like links) or full (all 18 reals; the default schedule).
+// rebuilt on load) or full (all 18 reals; the default schedule).
 //
 // Pass B (force_from_staples) builds every staple of the link (k, rho) from
 // those fields.  With S = S^{(rho)} and A_b = link(k, b), B_b = link(k+rho, b),
@@ -70,14 +70,15 @@ template <typename R> __device__ __forceinline__ R scalar(const KernelScalars &s
 }
 
 // Storage of the 24 staple planes: compact (rows 0 and 1, 12 reals, the
-// third row rebuilt on load, in the link layout) or full (all 18 reals,
-// nothing rebuilt).  Full planes are cut into blocks of 32 consecutive sites:
-// inside a block, 16-byte lane q (q < NW = 18/W) of the staple of site s is
-// at q*512 + s*16 bytes, and in FP32 its last two reals at NW*512 + s*8 --
-// 72 bytes per staple in FP32, 144 in FP64, every access 16- or 8-byte
-// aligned, and the lanes of one staple a constant 512 bytes apart, so that a
-// staple costs one address computation (plus one for the FP32 tail) however
-// many lanes it has.  Plane P starts at P * plane_bytes, plane_bytes = the
+// third row rebuilt on load) or full (all 18 reals, nothing rebuilt).  Both
+// are cut into blocks of 32 consecutive sites: inside a block, 16-byte lane
+// q (q < NW = 12/W compact, 18/W full) of the staple of site s is at
+// q*512 + s*16 bytes, and for full FP32 staples the last two reals at
+// NW*512 + s*8 -- 72 bytes per full staple in FP32, 144 in FP64, every
+// access 16- or 8-byte aligned, and the lanes of one staple a constant 512
+// bytes apart, so that a staple costs one address computation (plus one for
+// the FP32 tail) however many lanes it has.  Plane P starts at
+// P * plane_bytes, plane_bytes = the
 // 32-site blocks of the lattice (V rounded up to 32) times the block size.
 // Pass A writes them with evict-first stores: the 3.6 GB (at 32^3x64) would
 // otherwise push the links that pass A re-reads out of L2.
@@ -99,21 +100,78 @@ size_t full_plane_bytes(int64_t V, int precision)
     return (size_t)((V + 31) / 32) * blk;
 }
 
+// Compact planes: the first two rows (12 reals) of every staple, the third
+// rebuilt on load, in the same 32-site blocks (lane q, q < 12/W, of site s at
+// q*512 + s*16).
+template <typename R> struct CompactBlock {
+    using V4 = typename Vec<R>::type;
+    static constexpr int W = Vec<R>::W;
+    static constexpr int NW = 12 / W;
+    static constexpr int LANE = 32 * 16;
+    static constexpr int BYTES = NW * LANE;
+};
+
 template <typename R, bool FULL> struct Planes;
 
-// Compact planes: plane P is laid out like the links of direction P.
 template <typename R> struct Planes<R, false> {
-    R *sf;
-    int64_t V;
-    using Ref = int;
+    using B = CompactBlock<R>;
+    using V4 = typename B::V4;
+    char *base;
+    int64_t plane_bytes;
+    using Ref = char *;
 
-    __device__ __forceinline__ Ref at(int n) const { return n; }
-
-    __device__ __forceinline__ Mat<R> load(Ref n, int plane) const { return load_link(sf, V, plane, n); }
-
-    __device__ __forceinline__ void store(Ref n, int plane, const Mat<R> &u) const
+    __device__ __forceinline__ Ref at(int n) const
     {
-        store_link(sf, V, plane, n, u);
+        return base + (int64_t)(n >> 5) * B::BYTES + (n & 31) * 16;
+    }
+
+    __device__ __forceinline__ Mat<R> load(Ref r, int plane) const
+    {
+        const V4 *p = reinterpret_cast<const V4 *>(r + (int64_t)plane * plane_bytes);
+        R x[12];
+#pragma unroll
+        for (int q = 0; q < B::NW; ++q) {
+            const V4 v = __ldg(p + q * (B::LANE / 16));
+            if constexpr (B::W == 4) {
+                x[4 * q + 0] = v.x;
+                x[4 * q + 1] = v.y;
+                x[4 * q + 2] = v.z;
+                x[4 * q + 3] = v.w;
+            } else {
+                x[2 * q + 0] = v.x;
+                x[2 * q + 1] = v.y;
+            }
+        }
+        Mat<R> u;
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                u.re[i][j] = x[6 * i + 2 * j];
+                u.im[i][j] = x[6 * i + 2 * j + 1];
+            }
+        rebuild_row2(u);
+        return u;
+    }
+
+    __device__ __forceinline__ void store(Ref r, int plane, const Mat<R> &u) const
+    {
+        V4 *p = reinterpret_cast<V4 *>(r + (int64_t)plane * plane_bytes);
+        R x[12];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                x[6 * i + 2 * j] = u.re[i][j];
+                x[6 * i + 2 * j + 1] = u.im[i][j];
+            }
+#pragma unroll
+        for (int q = 0; q < B::NW; ++q) {
+            V4 v;
+            if constexpr (B::W == 4) v = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+            else v = make_double2(x[2 * q], x[2 * q + 1]);
+            __stcs(p + q * (B::LANE / 16), v);
+        }
     }
 };
 
@@ -199,7 +257,8 @@ template <typename R, bool FULL> __device__ __forceinline__ Planes<R, FULL> plan
         return Planes<R, true>{static_cast<char *>(L.staples), L.plane_bytes};
     } else {
         const int64_t V = (int64_t)L.dims[0] * L.dims[1] * L.dims[2] * L.dims[3];
-        return Planes<R, false>{static_cast<R *>(L.staples), V};
+        return Planes<R, false>{static_cast<char *>(L.staples),
+                                ((V + 31) / 32) * CompactBlock<R>::BYTES};
     }
 }
 
@@ -653,7 +712,8 @@ unsigned grid_of(int64_t items)
 // The process-wide choice per precision is set by lqcd_set_force_variant or
 // lqcd_autotune_force; -1 means the default: x rows with full staples, in
 // FP32 with the 4-CTA register cap (at 32^3x64: FP32 3.62 ms, 3.65 uncapped,
-// 4.28 with compact staples; FP64 110 vs 128 ms).
+// 3.83 with compact staples -- 4.28 when compact planes were laid out like
+// the links; FP64 110 vs 128 ms).
 constexpr int kSfVariants = 7;
 
 bool full_staples(int variant) { return variant >= 4; }
@@ -767,7 +827,6 @@ cudaError_t launch_pass_b_batched(const SfBatch &B, const KernelScalars &sc, int
     } else if (variant == 5) {
         auto k = force_from_staples_batched<R, ACTION, false, true, true>;
         k<<<persistent_grid(k, grid_slot(3, f64, ACTION, false), B.total), kBlock, 0, st>>>(B, sc);
-
     } else {
         auto k = force_from_staples_batched<R, ACTION, false>;
         k<<<persistent_grid(k, grid_slot(0, f64, ACTION, false), B.total), kBlock, 0, st>>>(B, sc);
