@@ -16,7 +16,8 @@ exchange step on one lattice per GPU); value = links of all ranks / max time.
 --impl reference times the FP64 CPU oracle on the host cores instead.
 --profile-force WORKLOAD runs only W + K FP32 force calls (the staple-field
 force with the fused momentum step and action) on that workload (a key of
-synth.WORKLOADS, e.g. 16^3x32) and prints their mean time: the small case
+synth.WORKLOADS, e.g. 16^3x32, or extents such as 32x16x16x16, drawn like
+the 32^3x64 workload) and prints their mean time: the small case
 that profiler captures run.  --profile-wilson WORKLOAD does the same for the
 FP32 Wilson hopping operator and hopping-term force.
 """
@@ -706,6 +707,19 @@ def run_ours(args):
     return 0
 
 
+def _named_or_explicit_workload(name):
+    """A workload of synth.WORKLOADS by name, or explicit extents "AxBxCxD"
+    drawn like the 32^3x64 workload (sigma 0.3, u0 0.87, beta 6, seed 0)."""
+    from paper_1808_02281_gb300 import synth
+
+    if name in synth.WORKLOADS:
+        return synth.WORKLOADS[name]
+    dims = tuple(int(d) for d in name.lower().split("x"))
+    if len(dims) != 4 or min(dims) < 1:
+        raise SystemExit(f"unknown workload {name!r}: a name of synth.WORKLOADS or AxBxCxD")
+    return dict(dims=dims, sigma=0.3, u0=0.87, beta=6.0, seed=0)
+
+
 def run_profile_force(args):
     """W + K FP32 force calls (staple planes, force pass with the fused
     momentum step and action) on one workload, for profiler captures of a
@@ -716,7 +730,7 @@ def run_profile_force(args):
     from paper_1808_02281_gb300 import lqcd, synth
 
     B.build()
-    w = synth.WORKLOADS[args.profile_force]
+    w = _named_or_explicit_workload(args.profile_force)
     dims = w["dims"]
     lat = lqcd.Lattice.symanzik(dims, w["beta"], w["u0"], "f32")
     U = lqcd.links_from_omega(lat, lqcd.algebra_to_device(lat, synth.omega(dims, w["sigma"], w["seed"])))
@@ -782,10 +796,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--force-variant", type=int, default=-1,
-                    help="fix the staple-field force schedule (0..6) instead of autotuning it "
+                    help="fix the staple-field force schedule (0..8) instead of autotuning it "
                          "at set-up; -1 (default) autotunes")
     ap.add_argument("--profile-force", default=None, metavar="WORKLOAD",
-                    help="only time FP32 force calls on this workload (profiler captures)")
+                    help="only time FP32 force calls on this workload, a name of "
+                         "synth.WORKLOADS or extents AxBxCxD (profiler captures)")
     ap.add_argument("--profile-wilson", default=None, metavar="WORKLOAD",
                     help="only time the FP32 Wilson kernels on this workload (profiler captures)")
     args = ap.parse_args()

@@ -351,7 +351,7 @@ int lqcd_get_force_variant(const lqcd_desc *desc)
     const int s = check_desc(desc);
     if (s) return s;
     const bool sf = desc->force_algo == LQCD_FORCE_AUTO || desc->force_algo == LQCD_FORCE_STAPLE_FIELDS;
-    return sf ? lqcd::staple_force_variant(desc->precision) : 0;
+    return sf ? lqcd::staple_force_variant(desc->precision, desc->dims) : 0;
 }
 
 int lqcd_set_force_variant(const lqcd_desc *desc, int variant)

@@ -384,6 +384,30 @@ __device__ __forceinline__ double block_sum(double v)
     return s;
 }
 
+// block_sum over the four warps of row group `row` of a CTA of ROWS groups
+// (named barrier 1 + row over its 128 threads; same order of summation).
+template <int ROWS> __device__ __forceinline__ double group_sum(double v, int row)
+{
+    if constexpr (ROWS == 1) {
+        return block_sum(v);
+    } else {
+        __shared__ double part[ROWS * kBlock / 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if (lane == 0) part[warp] = v;
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + row), "r"(kBlock) : "memory");
+        double s = 0.0;
+        if ((warp & 3) == 0) {
+            s = lane < kBlock / 32 ? part[warp + lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        }
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + row), "r"(kBlock) : "memory");
+        return s;
+    }
+}
+
 // Next virtual block for a persistent CTA of a batched launch, taken from a
 // work counter: the blocks in flight stay a contiguous window of the sweep
 // (as with hardware block scheduling), which keeps the L2 reuse of the
@@ -611,7 +635,7 @@ template <typename R, bool ACTION, bool UNROLLQ, bool FULL, bool DIRECT>
 __device__ __forceinline__ double force_block(const SfLattice &L, const KernelScalars &sc,
                                               const G32 &g, const Sweep &sw, int vb)
 {
-    const int rho = (int)(threadIdx.x >> 5);
+    const int rho = (int)((threadIdx.x >> 5) & 3);
     const int j = vb * 32 + (int)(threadIdx.x & 31);
     if (j >= g.V) return 0.0;
     const Coord c = swept_site(sw, j);
@@ -631,19 +655,27 @@ template <typename R, bool ACTION, bool DENSE> constexpr int min_blocks()
 // DIRECT products by default for full FP64 planes (see acc_su3).
 template <typename R, bool FULL> constexpr bool direct_default() { return FULL && sizeof(R) == 8; }
 
+// ROWS > 1: a CTA of ROWS groups of four warps on consecutive virtual
+// blocks (y-neighbouring x rows of the sweep), so that the staples of a
+// row's +-y neighbours are the own-row staples of another group of the CTA.
 template <typename R, bool ACTION, bool UNROLLQ, bool DENSE = false, bool FULL = false,
-          bool DIRECT = direct_default<R, FULL>()>
-__global__ void __launch_bounds__(kBlock, (min_blocks<R, ACTION, DENSE>()))
+          bool DIRECT = direct_default<R, FULL>(), int ROWS = 1>
+__global__ void __launch_bounds__(ROWS * kBlock, (min_blocks<R, ACTION, DENSE>() / ROWS > 0
+                                                       ? min_blocks<R, ACTION, DENSE>() / ROWS
+                                                       : 1))
     force_from_staples(const __grid_constant__ SfLattice L, const __grid_constant__ KernelScalars sc)
 {
     const G32 g = make_g32(L.dims);
     const Sweep sw = make_sweep(L, g);
     const int nvb = (int)virtual_blocks(g.V);
-    for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
-        const double acc = force_block<R, ACTION, UNROLLQ, FULL, DIRECT>(L, sc, g, sw, vb);
+    const int row = ROWS == 1 ? 0 : (int)(threadIdx.x >> 7);
+    for (int vb0 = blockIdx.x * ROWS; vb0 < nvb; vb0 += gridDim.x * ROWS) {
+        const int vb = vb0 + row;
+        double acc = 0.0;
+        if (vb < nvb) acc = force_block<R, ACTION, UNROLLQ, FULL, DIRECT>(L, sc, g, sw, vb);
         if constexpr (ACTION) {
-            const double s = block_sum(acc);
-            if (threadIdx.x == 0) L.partials[vb] = s;
+            const double s = group_sum<ROWS>(acc, row);
+            if ((threadIdx.x & (kBlock - 1)) == 0 && vb < nvb) L.partials[vb] = s;
         }
     }
 }
@@ -709,12 +741,27 @@ unsigned grid_of(int64_t items)
 //      4.45 ms with 64x16x16 at 32^3x64 FP32)
 //   5  as 4, registers capped for 4 CTAs/SM
 //   6  as 4 with spatial blocks up to 64x16x16
+//   7  as 5 in CTAs of two groups of four warps on consecutive virtual
+//      blocks: with x extent 32 those are y-neighbouring x rows, and a row's
+//      +-y staples are the other group's own staples (L1 hits)
+//   8  as 7 with spatial blocks up to 64x16x8
 // The process-wide choice per precision is set by lqcd_set_force_variant or
-// lqcd_autotune_force; -1 means the default: x rows with full staples, in
-// FP32 with the 4-CTA register cap (at 32^3x64: FP32 3.62 ms, 3.65 uncapped,
-// 3.83 with compact staples -- 4.28 when compact planes were laid out like
-// the links; FP64 110 vs 128 ms).
-constexpr int kSfVariants = 7;
+// lqcd_autotune_force; -1 means the default (default_variant).
+constexpr int kSfVariants = 9;
+
+// Built-in choice: full staples with the 4-CTA register cap in FP32, and
+// two-row CTAs where they measured faster -- x extent 32 and at least 2^20
+// sites (32^3x64: 3.54 against 3.67 ms, 32^4: 1.79 against 1.84 ms; but
+// 3.93 against 3.75 ms at 64x32^3, 0.25 against 0.24 ms at 16^3x32 and at
+// 32x16^3, and slower at 48^3x96, where warps straddle x rows); full
+// staples uncapped in FP64 (110 against 128 ms with compact ones; two-row
+// CTAs 110.5).
+int default_variant(int precision, const int dims[4])
+{
+    if (precision == LQCD_F64) return 4;
+    const int64_t V = (int64_t)dims[0] * dims[1] * dims[2] * dims[3];
+    return (dims[0] == 32 && V >= ((int64_t)1 << 20)) ? 8 : 5;
+}
 
 bool full_staples(int variant) { return variant >= 4; }
 
@@ -725,7 +772,6 @@ int grid_slot(int kind, bool f64, bool action, bool unrolled)
 {
     return kind * 8 + (f64 ? 4 : 0) + (action ? 2 : 0) + (unrolled ? 1 : 0);
 }
-constexpr int kSfDefault[2] = {5, 4};
 std::atomic<int> g_sf_variant[2] = {{-1}, {-1}};
 
 // Largest divisor of L not above cap.
@@ -738,10 +784,11 @@ int block_extent(int L, int cap)
 
 void set_traversal(SfLattice &L, int variant)
 {
-    const int cap_yz = (variant == 4 || variant == 5) ? 8 : 16;
+    const int cap_y = (variant == 4 || variant == 5 || variant == 7) ? 8 : 16;
+    const int cap_z = (variant >= 4 && variant != 6) ? 8 : 16;
     L.sweep[0] = block_extent(L.dims[0], 64);
-    L.sweep[1] = block_extent(L.dims[1], cap_yz);
-    L.sweep[2] = block_extent(L.dims[2], cap_yz);
+    L.sweep[1] = block_extent(L.dims[1], cap_y);
+    L.sweep[2] = block_extent(L.dims[2], cap_z);
     if (variant >= 2) {
         L.micro[0] = L.sweep[0];
         L.micro[1] = L.micro[2] = 1;
@@ -770,7 +817,7 @@ int resolve_variant(const ForceArgs &a)
     if (a.variant >= 0 && a.variant < kSfVariants) return a.variant;
     const int p = a.precision == LQCD_F64 ? 1 : 0;
     const int v = g_sf_variant[p].load();
-    return v < 0 ? kSfDefault[p] : v;
+    return v < 0 ? default_variant(a.precision, a.dims) : v;
 }
 
 // CTAs of a persistent launch: as many as are resident on the device at
@@ -798,7 +845,8 @@ template <typename K> unsigned persistent_grid(K kernel, int slot, int64_t work)
 template <typename R, bool ACTION>
 cudaError_t launch_pass_b(const SfLattice &L, const KernelScalars &sc, int variant, cudaStream_t st)
 {
-    const unsigned grid = grid_of(virtual_blocks((int64_t)L.dims[0] * L.dims[1] * L.dims[2] * L.dims[3]));
+    const int64_t V = (int64_t)L.dims[0] * L.dims[1] * L.dims[2] * L.dims[3];
+    const unsigned grid = grid_of(virtual_blocks(V));
     if (variant == 1) force_from_staples<R, ACTION, true><<<grid, kBlock, 0, st>>>(L, sc);
     else if (variant == 3) force_from_staples<R, ACTION, false, true><<<grid, kBlock, 0, st>>>(L, sc);
     else if (variant == 4 || variant == 6)
@@ -806,6 +854,9 @@ cudaError_t launch_pass_b(const SfLattice &L, const KernelScalars &sc, int varia
 
     else if (variant == 5)
         force_from_staples<R, ACTION, false, true, true><<<grid, kBlock, 0, st>>>(L, sc);
+    else if (variant >= 7)
+        force_from_staples<R, ACTION, false, true, true, direct_default<R, true>(), 2>
+            <<<grid_of((virtual_blocks(V) + 1) / 2), 2 * kBlock, 0, st>>>(L, sc);
     else force_from_staples<R, ACTION, false><<<grid, kBlock, 0, st>>>(L, sc);
     return cudaGetLastError();
 }
@@ -824,7 +875,7 @@ cudaError_t launch_pass_b_batched(const SfBatch &B, const KernelScalars &sc, int
     } else if (variant == 4 || variant == 6) {
         auto k = force_from_staples_batched<R, ACTION, false, false, true>;
         k<<<persistent_grid(k, grid_slot(2, f64, ACTION, false), B.total), kBlock, 0, st>>>(B, sc);
-    } else if (variant == 5) {
+    } else if (variant == 5 || variant >= 7) {
         auto k = force_from_staples_batched<R, ACTION, false, true, true>;
         k<<<persistent_grid(k, grid_slot(3, f64, ACTION, false), B.total), kBlock, 0, st>>>(B, sc);
     } else {
@@ -941,11 +992,11 @@ cudaError_t launch_force_staple_fields_batched(const ForceArgs &a, int n, const 
 
 int staple_force_variants() { return kSfVariants; }
 
-int staple_force_variant(int precision)
+int staple_force_variant(int precision, const int dims[4])
 {
     const int p = precision == LQCD_F64 ? 1 : 0;
     const int v = g_sf_variant[p].load();
-    return v < 0 ? kSfDefault[p] : v;
+    return v < 0 ? default_variant(precision, dims) : v;
 }
 
 void set_staple_force_variant(int precision, int variant)

@@ -102,7 +102,7 @@ cudaError_t launch_force_staple_fields(const ForceArgs &a, cudaStream_t st);
 cudaError_t launch_force_staple_fields_batched(const ForceArgs &a, int n, const SfLattice *items,
                                                unsigned long long *counter, cudaStream_t st);
 int staple_force_variants();
-int staple_force_variant(int precision);
+int staple_force_variant(int precision, const int dims[4]); // current choice (default by shape)
 void set_staple_force_variant(int precision, int variant);
 
 // The 34 loops of the action kernel: cls, len (4 or 6), signed directions.

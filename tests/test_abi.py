@@ -222,3 +222,26 @@ def test_batch_argument_checks(lib):
     need = lib.lqcd_workspace_bytes_batched(ctypes.byref(d), 2, refs)
     assert need == 2 * lib.lqcd_workspace_bytes_batched(ctypes.byref(d), 1, refs) - 256
     assert need >= 2 * 24 * 12 * 256 * 4
+
+
+def test_default_force_schedule_follows_the_lattice_shape(lib):
+    """The built-in staple-field schedule (no lqcd_set_force_variant, no
+    autotuning): two-row CTAs only for x extent 32 and at least 2^20 sites
+    in FP32, full staples with the register cap otherwise, uncapped full
+    staples in FP64; a set choice overrides it for every shape.  Host logic
+    only (no CUDA call)."""
+    cases = [((32, 32, 32, 64), "f32", 8), ((32, 32, 32, 32), "f32", 8),
+             ((32, 16, 16, 16), "f32", 5), ((16, 16, 16, 32), "f32", 5),
+             ((64, 32, 32, 32), "f32", 5), ((48, 48, 48, 96), "f32", 5),
+             ((32, 32, 32, 64), "f64", 4), ((4, 4, 4, 4), "f64", 4)]
+    for dims, prec, want in cases:
+        lat = lqcd.Lattice.symanzik(dims, precision=prec)
+        assert lqcd.force_variant_count(lat) == 9
+        assert lqcd.get_force_variant(lat) == want, (dims, prec)
+    lat = lqcd.Lattice.symanzik((16, 16, 16, 32))
+    try:
+        lqcd.set_force_variant(lat, 7)
+        assert lqcd.get_force_variant(lqcd.Lattice.symanzik((32, 32, 32, 64))) == 7
+    finally:
+        lqcd.set_force_variant(lat, -1)
+    assert lqcd.get_force_variant(lqcd.Lattice.symanzik((32, 32, 32, 64))) == 8
