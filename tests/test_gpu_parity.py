@@ -68,6 +68,8 @@ CASES = [
     ((5, 1, 3, 2), 0.4, 0.87),       # extent 1 in one direction
     ((1, 1, 1, 1), 0.6, 0.87),       # a single site: every loop wraps onto itself
     ((8, 6, 12, 4), 0.4, 0.87),      # sweep blocks of 8x6x6: two z blocks, extents not powers of 2
+    ((32, 3, 1, 3), 0.4, 0.87),      # x rows of 32: two-row CTAs pair y neighbours; 9 virtual
+                                     # blocks, so the last two-row CTA has an idle group
 ]
 
 
