@@ -176,6 +176,16 @@ cudaError_t launch_gaussian_momenta(const MdArgs &a, cudaStream_t st);
 
 // Wilson fermion hopping term (Sec. III).  Spinor fields: 24 reals per site,
 // real r = 2*(3*alpha + a) + (0 re, 1 im) of site n at ((r/W)*V + n)*W + r%W.
+// Unsigned division of n < 2^31 by an invariant d >= 1 (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", 1994):
+// t = mulhi(m, n), n / d = (t + ((n - t) >> sh1)) >> sh2 with l = ceil(log2 d),
+// m = floor(2^32 (2^l - d) / d) + 1, sh1 = min(l, 1), sh2 = max(l - 1, 0).
+struct DivMagic {
+    unsigned m;
+    int sh1, sh2;
+};
+DivMagic div_magic(unsigned d);
+
 struct WilsonArgs {
     int dims[4];
     int precision;
@@ -190,6 +200,9 @@ struct WilsonArgs {
     // the same four scalars rounded to FP32 by the launcher, so that FP32
     // kernels spend no FP64 conversions on them
     float fca, fcb, fcoef, fdt;
+    // division of a site index (below 2^31) by the strides L0, L0 L1,
+    // L0 L1 L2 as a multiply-high and shifts (set by the launcher)
+    DivMagic div[3];
 };
 cudaError_t launch_wilson_dslash(const WilsonArgs &a, cudaStream_t st);
 // FMA issue rate of the device in TFLOP/s (synchronises); scratch >= fma_rate_scratch_bytes().

@@ -93,6 +93,27 @@ template <typename I> __device__ __forceinline__ Sites<I> make_sites(const int d
     return g;
 }
 
+__device__ __forceinline__ unsigned div_by(unsigned n, const DivMagic &d)
+{
+    const unsigned t = __umulhi(d.m, n);
+    return (t + ((n - t) >> d.sh1)) >> d.sh2;
+}
+
+// Coordinates of site n < 2^31 with the strides' division magic (three
+// multiply-highs instead of three divisions by run-time values: hopping
+// force 0.242 -> 0.234 ms at 32^3x64 FP32).
+__device__ __forceinline__ Coord coord_fast(const Sites<int> &g, const DivMagic div[3], int n)
+{
+    Coord x;
+    x.c3 = (int)div_by((unsigned)n, div[2]);
+    int r = n - x.c3 * g.s3;
+    x.c2 = (int)div_by((unsigned)r, div[1]);
+    r -= x.c2 * g.s2;
+    x.c1 = (int)div_by((unsigned)r, div[0]);
+    x.c0 = r - x.c1 * g.s1;
+    return x;
+}
+
 template <typename I> __device__ __forceinline__ Coord coord_in(const Sites<I> &g, I n)
 {
     Coord x;
@@ -319,10 +340,12 @@ __device__ __forceinline__ void hop_x_shuffled(Spinor<R> &acc, const R *__restri
 
 constexpr int kDslashBlock = 128;
 
-// Register cap: 4 blocks (16 warps) per SM in FP32, measured 17 % faster at
-// 32^3x64 than the uncapped 138 registers (12 warps), without spills; FP64
-// is bound by the FP64 pipe and keeps its registers.
-template <typename R> constexpr int dslash_min_blocks() { return sizeof(R) == 8 ? 1 : 4; }
+// Register cap: 5 blocks (20 warps, 96 registers, a 64-byte spill) per SM in
+// FP32: at 32^3x64 0.161 against 0.167 ms with 4 blocks (128 registers) and
+// 0.245 ms with the uncapped 138 (12 warps) -- the kernel waits on loads, so
+// warps in flight count more than the spill; FP64 is bound by the FP64 pipe
+// and keeps its registers.
+template <typename R> constexpr int dslash_min_blocks() { return sizeof(R) == 8 ? 1 : 5; }
 
 // out_n = ca x_n + cb (calD x)_n, one thread per site.
 // XSHFL: x hops by shuffles.
@@ -338,7 +361,9 @@ __global__ void __launch_bounds__(kDslashBlock, dslash_min_blocks<R>())
     const R ca = scalar_of<R>(a.ca, a.fca), cb = scalar_of<R>(a.cb, a.fcb);
     const bool with_x = a.ca != 0.0;
     for (I n = (I)blockIdx.x * blockDim.x + threadIdx.x; n < g.V; n += (I)gridDim.x * blockDim.x) {
-        const Coord c = coord_in(g, n);
+        Coord c;
+        if constexpr (sizeof(I) == 4) c = coord_fast(g, a.div, n);
+        else c = coord_in(g, n);
         Spinor<R> acc;
 #pragma unroll
         for (int al = 0; al < 4; ++al)
@@ -409,7 +434,9 @@ __global__ void __launch_bounds__(kForceBlock) wilson_hopping_force(const __grid
     const int rho = (int)(threadIdx.x >> 5);
     const I ks = (I)blockIdx.x * 32 + (I)(threadIdx.x & 31);
     if (ks >= g.V) return;
-    const Coord c = coord_in(g, ks);
+    Coord c;
+    if constexpr (sizeof(I) == 4) c = coord_fast(g, a.div, ks);
+    else c = coord_in(g, ks);
     const int64_t V = g.V, k = ks, kp = (int64_t)(ks + hop_offset(g, c, rho, 1));
     Mat<R> m;
     switch (rho) {
@@ -444,8 +471,14 @@ unsigned blocks_for(int64_t items, int per_block)
 // Site loops in int: n + grid stride stays below 2 V + a block.
 bool sites_fit_int(int64_t V) { return 2 * V + 1024 < ((int64_t)1 << 31); }
 
-WilsonArgs with_float_scalars(WilsonArgs a)
+// The launch copy of the arguments: FP32 scalars and the strides' division
+// magic filled in.
+WilsonArgs launch_args(WilsonArgs a)
 {
+    const int64_t s[3] = {a.dims[0], (int64_t)a.dims[0] * a.dims[1],
+                          (int64_t)a.dims[0] * a.dims[1] * a.dims[2]};
+    for (int i = 0; i < 3; ++i)
+        a.div[i] = div_magic(s[i] < ((int64_t)1 << 31) ? (unsigned)s[i] : 1u);
     a.fca = (float)a.ca;
     a.fcb = (float)a.cb;
     a.fcoef = (float)a.coef;
@@ -455,9 +488,20 @@ WilsonArgs with_float_scalars(WilsonArgs a)
 
 } // namespace
 
+DivMagic div_magic(unsigned d)
+{
+    int l = 0;
+    while (l < 32 && ((uint64_t)1 << l) < d) ++l;
+    DivMagic g;
+    g.m = (unsigned)((((uint64_t)1 << 32) * (((uint64_t)1 << l) - d)) / d + 1);
+    g.sh1 = l < 1 ? l : 1;
+    g.sh2 = l > 1 ? l - 1 : 0;
+    return g;
+}
+
 cudaError_t launch_wilson_dslash(const WilsonArgs &args, cudaStream_t st)
 {
-    const WilsonArgs a = with_float_scalars(args);
+    const WilsonArgs a = launch_args(args);
     const int64_t V = (int64_t)a.dims[0] * a.dims[1] * a.dims[2] * a.dims[3];
     const unsigned grid = blocks_for(V, kDslashBlock);
     // shuffled x hops need whole x rows in every warp: L0 divides 32 (then
@@ -482,7 +526,7 @@ cudaError_t launch_wilson_dslash(const WilsonArgs &args, cudaStream_t st)
 
 cudaError_t launch_wilson_hopping_force(const WilsonArgs &args, cudaStream_t st)
 {
-    const WilsonArgs a = with_float_scalars(args);
+    const WilsonArgs a = launch_args(args);
     const int64_t V = (int64_t)a.dims[0] * a.dims[1] * a.dims[2] * a.dims[3];
     const unsigned grid = blocks_for(V, 32);
     const bool i32 = sites_fit_int(V);
