@@ -284,14 +284,20 @@ __device__ __forceinline__ G32 make_g32(const int dims[4])
     return g;
 }
 
-__device__ __forceinline__ Coord coord32(const G32 &g, int n)
+// Slots of SfLattice::div (the magic of each run-time divisor).
+enum { DV_S1, DV_S2, DV_S3, DV_VOL, DV_SLICE, DV_MVOL, DV_MX, DV_MY, DV_NMX, DV_NMY, DV_NBX, DV_NBY };
+
+__device__ __forceinline__ int divi(int n, const DivMagic &d) { return (int)div_by((unsigned)n, d); }
+
+// Coordinates of site n (the divisions by the strides as multiply-highs).
+__device__ __forceinline__ Coord coord32(const G32 &g, const DivMagic *dm, int n)
 {
     Coord x;
-    x.c3 = n / g.s3;
+    x.c3 = divi(n, dm[DV_S3]);
     int r = n - x.c3 * g.s3;
-    x.c2 = r / g.s2;
+    x.c2 = divi(r, dm[DV_S2]);
     r -= x.c2 * g.s2;
-    x.c1 = r / g.s1;
+    x.c1 = divi(r, dm[DV_S1]);
     x.c0 = r - x.c1 * g.s1;
     return x;
 }
@@ -322,7 +328,8 @@ __device__ __forceinline__ int step32(const G32 &g, const Coord &x, int mu, int 
 struct Sweep {
     int bx, by, bz, mx, my, mz;
     int nbx, nby, nmx, nmy, mvol;
-    int slice, vol; // sites per block slice and per block
+    int slice, vol;     // sites per block slice and per block
+    const DivMagic *dm; // magic of vol, slice, mvol, mx, my, nmx, nmy, nbx, nby
 };
 
 __device__ __forceinline__ Sweep make_sweep(const SfLattice &L, const G32 &g)
@@ -334,30 +341,32 @@ __device__ __forceinline__ Sweep make_sweep(const SfLattice &L, const G32 &g)
     s.mx = L.micro[0];
     s.my = L.micro[1];
     s.mz = L.micro[2];
-    s.nbx = g.L0 / s.bx;
-    s.nby = g.L1 / s.by;
-    s.nmx = s.bx / s.mx;
-    s.nmy = s.by / s.my;
+    s.nbx = L.counts[0];
+    s.nby = L.counts[1];
+    s.nmx = L.counts[2];
+    s.nmy = L.counts[3];
     s.mvol = s.mx * s.my * s.mz;
     s.slice = s.bx * s.by * s.bz;
     s.vol = s.slice * g.L3;
+    s.dm = L.div;
     return s;
 }
 
 __device__ __forceinline__ Coord swept_site(const Sweep &s, int j)
 {
-    const int blk = j / s.vol;
+    const DivMagic *dm = s.dm;
+    const int blk = divi(j, dm[DV_VOL]);
     const int r = j - blk * s.vol;
     Coord c;
-    c.c3 = r / s.slice;
+    c.c3 = divi(r, dm[DV_SLICE]);
     const int r2 = r - c.c3 * s.slice;
-    const int mt = r2 / s.mvol, w = r2 - mt * s.mvol;
-    const int xin = w % s.mx, yin = (w / s.mx) % s.my, zin = w / (s.mx * s.my);
-    const int mxi = mt % s.nmx, myi = (mt / s.nmx) % s.nmy, mzi = mt / (s.nmx * s.nmy);
-    const int bxi = blk % s.nbx;
-    const int q = blk / s.nbx;
-    const int byi = q % s.nby;
-    const int bzi = q / s.nby;
+    const int mt = divi(r2, dm[DV_MVOL]), w = r2 - mt * s.mvol;
+    const int wq = divi(w, dm[DV_MX]), xin = w - wq * s.mx;
+    const int zin = divi(wq, dm[DV_MY]), yin = wq - zin * s.my;
+    const int mq = divi(mt, dm[DV_NMX]), mxi = mt - mq * s.nmx;
+    const int mzi = divi(mq, dm[DV_NMY]), myi = mq - mzi * s.nmy;
+    const int q = divi(blk, dm[DV_NBX]), bxi = blk - q * s.nbx;
+    const int bzi = divi(q, dm[DV_NBY]), byi = q - bzi * s.nby;
     c.c0 = bxi * s.bx + mxi * s.mx + xin;
     c.c1 = byi * s.by + myi * s.my + yin;
     c.c2 = bzi * s.bz + mzi * s.mz + zin;
@@ -468,7 +477,7 @@ __device__ __forceinline__ void staples_block(const SfLattice &L, const G32 &g, 
     const int mu = (int)(threadIdx.x >> 5);
     const int x = vb * 32 + (int)(threadIdx.x & 31);
     if (x >= g.V) return;
-    site_staples<R, FULL>(static_cast<const R *>(L.links), g, coord32(g, x), x, mu,
+    site_staples<R, FULL>(static_cast<const R *>(L.links), g, coord32(g, L.div, x), x, mu,
                                 planes_of<R, FULL>(L), x);
 }
 
@@ -797,6 +806,26 @@ void set_traversal(SfLattice &L, int variant)
         L.micro[1] = L.sweep[1] % 2 == 0 ? 2 : 1;
         L.micro[2] = L.sweep[2] % 2 == 0 ? 2 : 1;
     }
+    // the divisors of coord32 and swept_site (all below 2^31: V < 2^31)
+    const int *d = L.dims;
+    const int64_t slice = (int64_t)L.sweep[0] * L.sweep[1] * L.sweep[2];
+    const int64_t dv[12] = {d[0],
+                            (int64_t)d[0] * d[1],
+                            (int64_t)d[0] * d[1] * d[2],
+                            slice * d[3],
+                            slice,
+                            (int64_t)L.micro[0] * L.micro[1] * L.micro[2],
+                            L.micro[0],
+                            L.micro[1],
+                            L.sweep[0] / L.micro[0],
+                            L.sweep[1] / L.micro[1],
+                            d[0] / L.sweep[0],
+                            d[1] / L.sweep[1]};
+    for (int i = 0; i < 12; ++i) L.div[i] = div_magic((unsigned)(dv[i] > 0 ? dv[i] : 1));
+    L.counts[0] = (int)dv[DV_NBX];
+    L.counts[1] = (int)dv[DV_NBY];
+    L.counts[2] = (int)dv[DV_NMX];
+    L.counts[3] = (int)dv[DV_NMY];
 }
 
 KernelScalars make_scalars(const ForceArgs &a)

@@ -60,11 +60,38 @@ struct ForceArgs {
     int variant;       // staple-field force pass schedule; -1 = process-wide choice
 };
 
+// Unsigned division of n < 2^31 by an invariant d >= 1 (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", 1994):
+// t = mulhi(m, n), n / d = (t + ((n - t) >> sh1)) >> sh2 with l = ceil(log2 d),
+// m = floor(2^32 (2^l - d) / d) + 1, sh1 = min(l, 1), sh2 = max(l - 1, 0);
+// the quotient is div_by (su3.cuh).  Kernels take these for the run-time
+// extents they divide site indices by, instead of dividing.
+struct DivMagic {
+    unsigned m;
+    int sh1, sh2;
+};
+
+inline DivMagic div_magic(unsigned d)
+{
+    int l = 0;
+    while (l < 32 && ((uint64_t)1 << l) < d) ++l;
+    DivMagic g;
+    g.m = (unsigned)((((uint64_t)1 << 32) * (((uint64_t)1 << l) - d)) / d + 1);
+    g.sh1 = l < 1 ? l : 1;
+    g.sh2 = l > 1 ? l - 1 : 0;
+    return g;
+}
+
 // One lattice as the staple-field kernels see it (filled on the host).
 struct SfLattice {
     int dims[4];
     int sweep[3];      // spatial block extents of the pass-B traversal
     int micro[3];      // micro-tile extents inside a block slice
+    // division magic (set_traversal): site strides L0, L0 L1, L0 L1 L2, then
+    // the sweep's block volume, slice, micro-tile volume, micro-tile x and y
+    // extents, micro-tiles along x and y of a block, blocks along x and y
+    DivMagic div[12];
+    int counts[4];     // blocks along x and y, micro-tiles along x and y of a block
     int64_t vb_begin;  // batch: first virtual block of this lattice
     int64_t plane_bytes; // full staple planes: bytes of one plane
     const void *links;
@@ -176,15 +203,6 @@ cudaError_t launch_gaussian_momenta(const MdArgs &a, cudaStream_t st);
 
 // Wilson fermion hopping term (Sec. III).  Spinor fields: 24 reals per site,
 // real r = 2*(3*alpha + a) + (0 re, 1 im) of site n at ((r/W)*V + n)*W + r%W.
-// Unsigned division of n < 2^31 by an invariant d >= 1 (Granlund and
-// Montgomery, "Division by invariant integers using multiplication", 1994):
-// t = mulhi(m, n), n / d = (t + ((n - t) >> sh1)) >> sh2 with l = ceil(log2 d),
-// m = floor(2^32 (2^l - d) / d) + 1, sh1 = min(l, 1), sh2 = max(l - 1, 0).
-struct DivMagic {
-    unsigned m;
-    int sh1, sh2;
-};
-DivMagic div_magic(unsigned d);
 
 struct WilsonArgs {
     int dims[4];

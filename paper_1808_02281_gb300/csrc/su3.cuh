@@ -6,6 +6,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "kernels.h"
+
 namespace lqcd {
 
 // ---------------------------------------------------------------- types
@@ -540,6 +542,13 @@ __host__ __device__ __forceinline__ Geom make_geom(const int dims[4])
 struct Coord {
     int c0, c1, c2, c3;
 };
+
+// n / d for n < 2^31 with the magic of d (kernels.h: DivMagic).
+__device__ __forceinline__ unsigned div_by(unsigned n, const DivMagic &d)
+{
+    const unsigned t = __umulhi(d.m, n);
+    return (t + ((n - t) >> d.sh1)) >> d.sh2;
+}
 
 __device__ __forceinline__ Coord coord_of(const Geom &g, int64_t n)
 {

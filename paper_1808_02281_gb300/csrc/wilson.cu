@@ -93,12 +93,6 @@ template <typename I> __device__ __forceinline__ Sites<I> make_sites(const int d
     return g;
 }
 
-__device__ __forceinline__ unsigned div_by(unsigned n, const DivMagic &d)
-{
-    const unsigned t = __umulhi(d.m, n);
-    return (t + ((n - t) >> d.sh1)) >> d.sh2;
-}
-
 // Coordinates of site n < 2^31 with the strides' division magic (three
 // multiply-highs instead of three divisions by run-time values: hopping
 // force 0.242 -> 0.234 ms at 32^3x64 FP32).
@@ -487,17 +481,6 @@ WilsonArgs launch_args(WilsonArgs a)
 }
 
 } // namespace
-
-DivMagic div_magic(unsigned d)
-{
-    int l = 0;
-    while (l < 32 && ((uint64_t)1 << l) < d) ++l;
-    DivMagic g;
-    g.m = (unsigned)((((uint64_t)1 << 32) * (((uint64_t)1 << l) - d)) / d + 1);
-    g.sh1 = l < 1 ? l : 1;
-    g.sh2 = l > 1 ? l - 1 : 0;
-    return g;
-}
 
 cudaError_t launch_wilson_dslash(const WilsonArgs &args, cudaStream_t st)
 {
