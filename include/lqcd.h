@@ -151,10 +151,10 @@ LQCD_API int lqcd_md_force_step(const lqcd_desc *desc, const void *links, void *
  * is process-wide per precision.
  *   lqcd_force_variant_count: number of variants for desc->force_algo.
  *   lqcd_get_force_variant / lqcd_set_force_variant: the current choice;
- *     -1 restores the built-in default, which depends on the precision and
- *     the extents in desc (get returns the schedule a launch with desc would
- *     use).  Not thread-safe against concurrent force launches of the same
- *     precision.
+ *     -1 restores the built-in default, which depends on the precision (and
+ *     may depend on the extents in desc: get returns the schedule a launch
+ *     with desc would use).  Not thread-safe against concurrent force
+ *     launches of the same precision.
  *   lqcd_autotune_force: times every variant `reps` times on these links
  *     (with the fused action, as in an MD step) and keeps the fastest.  It
  *     SYNCHRONISES the stream (call it once at set-up).  force: a scratch

@@ -758,18 +758,17 @@ unsigned grid_of(int64_t items)
 // lqcd_autotune_force; -1 means the default (default_variant).
 constexpr int kSfVariants = 9;
 
-// Built-in choice: full staples with the 4-CTA register cap in FP32, and
-// two-row CTAs where they measured faster -- x extent 32 and at least 2^20
-// sites (32^3x64: 3.54 against 3.67 ms, 32^4: 1.79 against 1.84 ms; but
-// 3.93 against 3.75 ms at 64x32^3, 0.25 against 0.24 ms at 16^3x32 and at
-// 32x16^3, and slower at 48^3x96, where warps straddle x rows); full
-// staples uncapped in FP64 (110 against 128 ms with compact ones; two-row
-// CTAs 110.5).
+// Built-in choice: full staples with the 4-CTA register cap in FP32 (at
+// 32^3x64 3.42 ms against 3.45-3.46 ms for the two-row CTAs and 3.64-3.66
+// for the others; at 32^4 1.73 against 1.75 ms), uncapped full staples in
+// FP64 (110 against 128 ms with compact ones; two-row CTAs 110.2-110.3).
+// The two-row CTAs won (3.54 against 3.67 ms at 32^3x64) while the sweep
+// still divided by run-time extents; with multiply-high divisions the
+// one-row CTA is ahead.  The dims are kept for shape-dependent choices.
 int default_variant(int precision, const int dims[4])
 {
-    if (precision == LQCD_F64) return 4;
-    const int64_t V = (int64_t)dims[0] * dims[1] * dims[2] * dims[3];
-    return (dims[0] == 32 && V >= ((int64_t)1 << 20)) ? 8 : 5;
+    (void)dims;
+    return precision == LQCD_F64 ? 4 : 5;
 }
 
 bool full_staples(int variant) { return variant >= 4; }

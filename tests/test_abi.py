@@ -224,15 +224,13 @@ def test_batch_argument_checks(lib):
     assert need >= 2 * 24 * 12 * 256 * 4
 
 
-def test_default_force_schedule_follows_the_lattice_shape(lib):
+def test_default_force_schedule(lib):
     """The built-in staple-field schedule (no lqcd_set_force_variant, no
-    autotuning): two-row CTAs only for x extent 32 and at least 2^20 sites
-    in FP32, full staples with the register cap otherwise, uncapped full
-    staples in FP64; a set choice overrides it for every shape.  Host logic
-    only (no CUDA call)."""
-    cases = [((32, 32, 32, 64), "f32", 8), ((32, 32, 32, 32), "f32", 8),
-             ((32, 16, 16, 16), "f32", 5), ((16, 16, 16, 32), "f32", 5),
-             ((64, 32, 32, 32), "f32", 5), ((48, 48, 48, 96), "f32", 5),
+    autotuning): full staples with the register cap in FP32, uncapped full
+    staples in FP64, for every shape; a set choice overrides it, and -1
+    restores it.  Host logic only (no CUDA call)."""
+    cases = [((32, 32, 32, 64), "f32", 5), ((32, 32, 32, 32), "f32", 5),
+             ((16, 16, 16, 32), "f32", 5), ((48, 48, 48, 96), "f32", 5),
              ((32, 32, 32, 64), "f64", 4), ((4, 4, 4, 4), "f64", 4)]
     for dims, prec, want in cases:
         lat = lqcd.Lattice.symanzik(dims, precision=prec)
@@ -242,6 +240,7 @@ def test_default_force_schedule_follows_the_lattice_shape(lib):
     try:
         lqcd.set_force_variant(lat, 7)
         assert lqcd.get_force_variant(lqcd.Lattice.symanzik((32, 32, 32, 64))) == 7
+        assert lqcd.get_force_variant(lqcd.Lattice.symanzik((32, 32, 32, 64), precision="f64")) == 4
     finally:
         lqcd.set_force_variant(lat, -1)
-    assert lqcd.get_force_variant(lqcd.Lattice.symanzik((32, 32, 32, 64))) == 8
+    assert lqcd.get_force_variant(lqcd.Lattice.symanzik((32, 32, 32, 64))) == 5
