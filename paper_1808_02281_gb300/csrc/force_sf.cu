@@ -431,6 +431,24 @@ __device__ __forceinline__ int64_t next_virtual_block(unsigned long long *counte
     return vb;
 }
 
+// The same queue with the next block claimed (by thread 0) when the current
+// one starts and handed to the block when it ends, so that the atomic's
+// latency overlaps the current block's work.
+__device__ __forceinline__ unsigned long long claim_virtual_block(unsigned long long *counter)
+{
+    return threadIdx.x == 0 ? atomicAdd(counter, 1ull) : 0ull;
+}
+
+__device__ __forceinline__ int64_t publish_virtual_block(unsigned long long claimed)
+{
+    __shared__ unsigned long long s_vb;
+    if (threadIdx.x == 0) s_vb = claimed;
+    __syncthreads();
+    const int64_t vb = (int64_t)s_vb;
+    __syncthreads();
+    return vb;
+}
+
 // Lattice of a batch that virtual block vb (global numbering) belongs to.
 __device__ __forceinline__ int batch_entry(const SfBatch &B, int64_t vb)
 {
@@ -492,11 +510,12 @@ __global__ void __launch_bounds__(kBlock) staple_fields(const __grid_constant__ 
 template <typename R, bool FULL>
 __global__ void __launch_bounds__(kBlock) staple_fields_batched(const __grid_constant__ SfBatch B)
 {
-    for (int64_t vb = next_virtual_block(B.counter); vb < B.total;
-         vb = next_virtual_block(B.counter)) {
+    for (int64_t vb = next_virtual_block(B.counter); vb < B.total;) {
+        const unsigned long long next = claim_virtual_block(B.counter);
         const int c = batch_entry(B, vb);
         const SfLattice &L = B.e[c];
         staples_block<R, FULL>(L, make_g32(L.dims), (int)(vb - L.vb_begin));
+        vb = publish_virtual_block(next);
     }
 }
 
@@ -695,8 +714,8 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<R, ACTION, DENSE>()))
     force_from_staples_batched(const __grid_constant__ SfBatch B,
                                const __grid_constant__ KernelScalars sc)
 {
-    for (int64_t vb = next_virtual_block(B.counter + 1); vb < B.total;
-         vb = next_virtual_block(B.counter + 1)) {
+    for (int64_t vb = next_virtual_block(B.counter + 1); vb < B.total;) {
+        const unsigned long long next = claim_virtual_block(B.counter + 1);
         const int c = batch_entry(B, vb);
         const SfLattice &L = B.e[c];
         const G32 g = make_g32(L.dims);
@@ -706,6 +725,7 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<R, ACTION, DENSE>()))
             const double s = block_sum(acc);
             if (threadIdx.x == 0) L.partials[vb - L.vb_begin] = s;
         }
+        vb = publish_virtual_block(next);
     }
 }
 
